@@ -1,0 +1,332 @@
+#!/usr/bin/env python3
+"""Throughput of AMS-sort on GB300: two-level sample sort of 2^28 uniform uint64 keys
+(r1 = r2 = 256 groups, overpartitioning b = 4), keys/s, per GPU or summed over ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ams|reference]
+                    [--workload two_level_u64|single_level_u32]
+
+One step sorts the whole input once (out of place, so every step sees the same
+unsorted input; the 2 GiB input and output exceed the L2 cache, so no flush is
+needed).  Under torchrun every rank sorts its own input (replicas, weak scaling).
+Prints one JSON line on rank 0.  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "keys/s & HBM-roofline frac at 2^28 u64; p50/p99 latency of mixed-size requests"
+WORKLOADS = {
+    "two_level_u64": dict(n=1 << 28, bits=64, kt=1, levels=2, buckets=[256, 256], b=4, a=0,
+                          dist="uniform", dtype="u64",
+                          desc="2-level AMS-sort, 2^28 uniform uint64 keys, r=256x256, b=4"),
+    "single_level_u32": dict(n=1 << 20, bits=32, kt=0, levels=1, buckets=[256], b=1, a=16,
+                             dist="uniform", dtype="u32",
+                             desc="1-level sample sort, 2^20 uniform uint32 keys, 256 buckets, a=16"),
+}
+KIND_BYTES = {"classify": 1, "scatter": 2, "basecase": 2}  # key passes per element
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _traffic(kind):
+    """DRAM bytes per launch of `kind` from the committed ncu summary, if the kernel
+    source has not changed since the capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)[kind]
+        src = os.path.join(ROOT, "paper_1410_6754_gb300", "csrc", t["source"])
+        with open(src, "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] != t["sha256_16"]:
+                return None
+        return float(t["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv",
+                                       "-lms", "100", "-i", str(gpu_index)],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.strip() for r in self.f.read().splitlines()[1:] if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            c = [x.strip() for x in r.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1].split()[0]))
+                mx.append(float(c[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, c[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def _gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [x.strip() for x in vis.split(",") if x.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return str(local_rank)
+
+
+def run_reference(args, wl):
+    """CPU oracle (single thread, numpy stable sort) on a bounded sample per step."""
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle as O
+    from paper_1410_6754_gb300 import inputs as I
+    full = wl["n"]
+    probe = I.generate(wl["dist"], 1 << 18, 0, wl["bits"])
+    t0 = time.perf_counter()
+    O.sort_keys(wl["kt"], probe)
+    per_key = (time.perf_counter() - t0) / len(probe)
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    m = int(min(full, max(1 << 16, budget / max(per_key, 1e-12))))
+    m = 1 << (m.bit_length() - 1)
+    sample = I.generate(wl["dist"], m, 0, wl["bits"])
+    for _ in range(args.warmup):
+        O.sort_keys(wl["kt"], sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.sort_keys(wl["kt"], sample)
+    dt = time.perf_counter() - t0
+    value = args.steps * m / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "keys/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": wl["dtype"], "data": "synthetic",
+        "config": {"workload": wl["desc"], "sample_keys_per_step": m},
+        "cpu_baseline": {"value": value, "unit": "keys/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{m} keys of the same workload per step (first {m} keys of the "
+                                   f"seeded input), numpy stable sort, one thread"},
+        "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _u64_order(t):
+    """int64 view of unsigned keys -> int64 whose signed order is the unsigned order."""
+    import torch
+    return t ^ torch.tensor(-(1 << 63), dtype=torch.int64, device=t.device)
+
+
+def _check_sorted(src, dst, bits):
+    """Output sorted and a permutation of the input (order-independent hash)."""
+    import torch
+    from paper_1410_6754_gb300.inputs import _mix_t
+    if bits == 64:
+        o = _u64_order(dst)
+        ok = bool((o[1:] >= o[:-1]).all())
+        hs = _mix_t(src).sum()
+        hd = _mix_t(dst).sum()
+    else:
+        o = dst.to(torch.int64) & 0xFFFFFFFF
+        ok = bool((o[1:] >= o[:-1]).all())
+        hs = _mix_t(src.to(torch.int64) & 0xFFFFFFFF).sum()
+        hd = _mix_t(o).sum()
+    return ok and bool(hs == hd)
+
+
+def run_ams(args, wl):
+    import torch
+    rank, world, local_rank = _dist_env()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    if rank == 0:
+        import __graft_entry__
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    import paper_1410_6754_gb300 as ams
+    from paper_1410_6754_gb300 import inputs as I
+
+    n, bits = wl["n"], wl["bits"]
+    src = I.generate(wl["dist"], n, rank, bits, device="cuda")
+    dst = torch.empty_like(src)
+    ctx = ams.Context()
+    kw = dict(levels=wl["levels"], buckets=wl["buckets"], seed=0, a=wl["a"], b=wl["b"], kt=wl["kt"])
+    for _ in range(args.warmup):
+        ctx.sort(src, dst, **kw)
+    ctx.sync()
+    if not _check_sorted(src, dst, bits):
+        print(json.dumps({"error": "output check failed"}), flush=True)
+        return 1
+    ctx.stats()  # reset the launch / event tallies
+    torch.cuda.synchronize()
+    sampler = ClockSampler(_gpu_index(local_rank))
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ctx.sort(src, dst, flags=ams.FLAG_PHASE_TIMERS, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    st = ctx.stats()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps * n / (ms * 1e-3)
+
+    # dominant kernel: algorithmic bytes per launch / average launch time
+    w = bits // 8
+    peak, peak_src = _peaks()
+    calls_per_step = {k: st["kernel_calls"][k] / max(1, args.steps) for k in st["kernel_calls"]}
+    dom = max(KIND_BYTES, key=lambda k: st["kernel_ms"][k])
+    avg_ms = st["kernel_ms"][dom] / max(1, st["kernel_calls"][dom])
+    bytes_per_launch = KIND_BYTES[dom] * w * st["kernel_elems"][dom] / max(1e-9, calls_per_step[dom])
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    step_bytes = (wl["levels"] + 1) * 2 * n * w
+    share = {k: round(st["kernel_ms"][k] / max(1e-9, sum(st["kernel_ms"].values())), 4)
+             for k in st["kernel_ms"]}
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if args.e2e_steps > 0:
+        host_src = src.cpu().pin_memory()
+        host = torch.empty_like(host_src).pin_memory()
+        times = []
+        for i in range(args.e2e_steps + 1):
+            host.copy_(host_src)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ams.sort_host(host, **kw)
+            times.append(time.perf_counter() - t0)
+        e2e_s = statistics.median(times[1:])
+        if dist:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * n / e2e_s, "unit": "keys/s", "h2d_bytes_per_step": n * w,
+               "d2h_bytes_per_step": n * w, "steps": args.e2e_steps,
+               "api": "ams_sort_host (pinned host buffers, copies inside the timed region)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        import oracle as O
+        m = 1 << 23
+        sample = src[:m].cpu().numpy().view("uint64" if bits == 64 else "uint32")
+        reps, t0 = 0, time.perf_counter()
+        while reps < 1 or (time.perf_counter() - t0 < args.cpu_seconds and reps < 8):
+            O.sort_keys(wl["kt"], sample)
+            reps += 1
+        dt = (time.perf_counter() - t0) / reps
+        cpu = {"value": m / dt, "unit": "keys/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {m} keys of the same input, numpy stable sort, one thread, "
+                         f"{reps} repetitions"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": wl["dtype"], "data": "synthetic",
+            "config": {"workload": wl["desc"], "n": n, "levels": wl["levels"],
+                       "buckets": wl["buckets"], "b": wl["b"], "a": wl["a"] or "ceil(1.6 log10 n)",
+                       "parallelism": f"replicas x{world}",
+                       "l2": "input 2^28 keys and output exceed L2; no flush"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": _traffic(dom),
+                         "peak_source": f"{peak_src} hbm copy bandwidth",
+                         "alg_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms},
+            "step_roofline": {"alg_bytes": step_bytes, "achieved_gbs": step_bytes / (ms / args.steps * 1e-3) / 1e9,
+                              "frac": step_bytes / (ms / args.steps * 1e-3) / 1e9 / peak,
+                              "definition": "(levels + 1) x (read + write) x n x key bytes per step"},
+            "kernel_share": share,
+            "kernel_avg_ms": {k: st["kernel_ms"][k] / max(1, st["kernel_calls"][k]) for k in st["kernel_ms"]},
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+            "gpu_launches": st["kernel_launches"],
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ams", choices=["ams", "reference"])
+    ap.add_argument("--workload", default="two_level_u64", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_ams(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,243 @@
+/*
+ * ams.h -- C ABI of libams: adaptive multi-level sample sort (AMS-sort) on one GPU.
+ *
+ * Method: Axtmann, Bingmann, Sanders, Schulz, "Practical Massively Parallel
+ * Sorting", SPAA 2015.  Problem statement: Section 1 (sort n elements; the output
+ * is a sorted permutation of the input).  Tie breaking: Section 2 and Appendix D
+ * (elements are ordered by (key, original position), which makes every key unique;
+ * the result is therefore the stable order).  Algorithm: Section 6 (random sample,
+ * sample sorted with the fast work-inefficient sort of Section 4.2, b*r-1 splitters
+ * of equidistant rank, partition into b*r buckets plus equality buckets, global
+ * bucket sizes, grouping of consecutive buckets with the scanning algorithm and its
+ * optimal bound, delivery, recursion, sequential base case).
+ *
+ * Conventions shared by every call:
+ *  - Pointers named d_* are device pointers (CUDA global memory of the current
+ *    device); pointers named h_* are host pointers.  The caller owns every buffer it
+ *    passes; the library owns its scratch memory (held by a context, see below).
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default stream.
+ *    Device calls are stream ordered and asynchronous: they return once the work is
+ *    enqueued.  Errors found on the host (bad arguments, allocation failure, launch
+ *    failure) are returned at once.  Errors found on the device (a table capacity
+ *    exceeded) are latched in the context and returned by ams_context_sync().
+ *  - Keys: AMS_U32 (uint32_t), AMS_U64 (uint64_t), AMS_F32 (float, ordered through
+ *    the order-preserving bit map: negative values have all bits flipped, others get
+ *    the sign bit set; hence -0.0 sorts before +0.0, NaNs with the sign bit set sort
+ *    first and the others last; output keys keep their input bit patterns).
+ *  - Payloads (pairs) are uint64_t and move with their key.
+ *  - The output is the unique permutation ordered by (key, original index).  It
+ *    does not depend on `seed`, `levels`, `buckets_per_level` or the options; those
+ *    only change the intermediate steps (sample, splitters, groups).
+ *  - n must be below 2^32.  levels is in [1, 8]; buckets_per_level has `levels`
+ *    host entries r_l >= 2 (groups per level); b * r_l (range buckets per level) must
+ *    lie in [2, 2048].  More levels than requested are added when n / prod(r_l)
+ *    still exceeds the base-case capacity (at most 8 levels in total).
+ *  - The library never aborts, traps or prints.
+ */
+#ifndef AMS_H
+#define AMS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define AMS_API __attribute__((visibility("default")))
+#else
+#define AMS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { AMS_U32 = 0, AMS_U64 = 1, AMS_F32 = 2 } ams_key_type;
+
+typedef enum {
+  AMS_OK = 0,
+  AMS_ERR_INVALID = 1,      /* bad argument (null pointer, sizes, parameters) */
+  AMS_ERR_OOM = 2,          /* device or pinned-host allocation failed */
+  AMS_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+  AMS_ERR_TIMEOUT = 4,      /* a bounded device wait gave up */
+  AMS_ERR_UNSUPPORTED = 5,  /* valid request outside this build's limits */
+  AMS_ERR_INTERNAL = 6      /* a device table overflowed (result not valid) */
+} ams_status;
+
+/* Tuning knobs; pass NULL for all defaults.  Zero in a field selects its default. */
+typedef struct ams_options {
+  uint32_t oversample_a;    /* a: 0 = per segment, ceil(1.6*log10(n_g)) (Section 7.2) */
+  uint32_t overpartition_b; /* b: 0 = 1 for levels == 1, else 4 (Section 6) */
+  uint32_t basecase_cap;    /* C: largest group sorted in shared memory;
+                               0 = 16384 for 32-bit keys, 8192 otherwise and for pairs */
+  uint32_t flags;           /* AMS_FLAG_* */
+} ams_options;
+
+#define AMS_FLAG_PHASE_TIMERS 0x1u  /* record CUDA events per kernel (see ams_stats) */
+
+/* --------------------------------------------------------------- whole sorts */
+
+/* Sort n keys in place (Section 1 output; Section 6 method). */
+AMS_API ams_status ams_sort_keys(void* d_keys, uint64_t n, ams_key_type kt, int levels,
+                         const uint32_t* buckets_per_level, uint64_t seed,
+                         const ams_options* opt, void* stream);
+
+/* Sort n (key, payload) pairs in place; payload i moves with key i. */
+AMS_API ams_status ams_sort_pairs(void* d_keys, uint64_t* d_vals, uint64_t n, ams_key_type kt,
+                          int levels, const uint32_t* buckets_per_level, uint64_t seed,
+                          const ams_options* opt, void* stream);
+
+/* Sort every segment [d_offsets[s], d_offsets[s+1]) independently, in place.
+ * d_offsets: device array of nseg+1 non-decreasing offsets with d_offsets[0] = 0
+ * and d_offsets[nseg] = n (the caller guarantees this; it is not checked).
+ * d_vals may be NULL (keys only). */
+AMS_API ams_status ams_sort_segmented(void* d_keys, uint64_t* d_vals, const uint64_t* d_offsets,
+                              uint64_t nseg, uint64_t n, ams_key_type kt, int levels,
+                              const uint32_t* buckets_per_level, uint64_t seed,
+                              const ams_options* opt, void* stream);
+
+/* Out-of-place forms: read d_in (not modified), write d_out (n elements).  d_in may
+ * equal d_out.  d_vals_in / d_vals_out may be NULL together (keys only). */
+AMS_API ams_status ams_sort_keys_into(const void* d_in, void* d_out, uint64_t n, ams_key_type kt,
+                              int levels, const uint32_t* buckets_per_level, uint64_t seed,
+                              const ams_options* opt, void* stream);
+AMS_API ams_status ams_sort_pairs_into(const void* d_keys_in, void* d_keys_out,
+                               const uint64_t* d_vals_in, uint64_t* d_vals_out, uint64_t n,
+                               ams_key_type kt, int levels, const uint32_t* buckets_per_level,
+                               uint64_t seed, const ams_options* opt, void* stream);
+
+/* Host-buffer form: copies h_keys (and h_vals if not NULL) to the device, sorts and
+ * copies the result back into the same host arrays.  Synchronous: returns after the
+ * result is in host memory (device errors included).  Pinned host memory makes the
+ * copies faster but is not required. */
+AMS_API ams_status ams_sort_host(void* h_keys, uint64_t* h_vals, uint64_t n, ams_key_type kt,
+                         int levels, const uint32_t* buckets_per_level, uint64_t seed,
+                         const ams_options* opt, void* stream);
+
+/* --------------------------------------------------------------- contexts */
+
+/* A context holds the scratch memory (ping-pong buffer, per-level tables), the
+ * device status word and the statistics of the last sort.  The calls above use a
+ * default context per device.  A context must not be used by two host threads at
+ * once, and sorts on one context must be ordered on one stream; use one context
+ * per concurrent stream.  hbm_budget_bytes caps the scratch the context may hold
+ * (0 = no cap); a sort that needs more returns AMS_ERR_OOM. */
+AMS_API ams_status ams_context_create(uint64_t hbm_budget_bytes, void** ctx);
+AMS_API ams_status ams_context_destroy(void* ctx);
+
+typedef struct ams_request {
+  const void* keys_in;          /* device */
+  void* keys_out;               /* device; may equal keys_in */
+  const uint64_t* vals_in;      /* device or NULL */
+  uint64_t* vals_out;           /* device or NULL (NULL iff vals_in is NULL) */
+  const uint64_t* d_offsets;    /* device, nseg+1 entries; NULL = one segment of n */
+  uint64_t nseg;
+  uint64_t n;
+  ams_key_type kt;
+  int levels;
+  const uint32_t* buckets_per_level;  /* host, `levels` entries */
+  uint64_t seed;
+  ams_options opt;
+} ams_request;
+
+/* The general entry point behind all sort calls.  ctx NULL = default context. */
+AMS_API ams_status ams_sort_request(void* ctx, const ams_request* req, void* stream);
+
+/* Wait for the context's last sort and return its device status (AMS_OK or
+ * AMS_ERR_INTERNAL / AMS_ERR_TIMEOUT). */
+AMS_API ams_status ams_context_sync(void* ctx);
+
+/* Bytes of device scratch the context holds now. */
+AMS_API uint64_t ams_context_scratch_bytes(void* ctx);
+
+typedef struct ams_stats {
+  uint32_t levels_planned;       /* distribution levels launched */
+  uint32_t kernel_launches;      /* kernels launched by the last sort */
+  uint32_t segments[8];          /* segments processed per level */
+  uint32_t basecase_items[9];    /* base-case work items per level (0 = before level 1) */
+  uint32_t device_status;
+  uint32_t pad;
+  /* With AMS_FLAG_PHASE_TIMERS: summed device time (ms) per kernel kind and the
+   * number of launches of that kind, for the last sort.  Kinds: */
+#define AMS_K_INIT 0
+#define AMS_K_SETUP 1
+#define AMS_K_SAMPLE_SORT 2   /* sample + local tile sort (Section 4.2) */
+#define AMS_K_CROSS_RANK 3    /* all-pairs tile ranking (Section 4.2) */
+#define AMS_K_SPLITTERS 4
+#define AMS_K_CLASSIFY 5      /* classify + count */
+#define AMS_K_SCAN 6
+#define AMS_K_BINPACK 7
+#define AMS_K_SCATTER 8
+#define AMS_K_BASECASE 9
+#define AMS_K_COUNT 10
+  float kernel_ms[AMS_K_COUNT];
+  uint32_t kernel_calls[AMS_K_COUNT];
+  uint64_t kernel_elems[AMS_K_COUNT];  /* elements read by that kind (for bandwidth) */
+} ams_stats;
+
+/* Statistics (waits for the context's last sort).  segments, basecase_items,
+ * kernel_elems and levels_planned describe the last sort; kernel_launches,
+ * kernel_ms and kernel_calls add up every sort since the previous call, which
+ * resets them.  ctx NULL = default context. */
+AMS_API ams_status ams_get_stats(void* ctx, ams_stats* out);
+
+/* --------------------------------------------------------------- building blocks
+ * Each step of one distribution level on one segment, as its own call.  They run the
+ * same kernels as the whole sort (on a one-segment table) and use the default
+ * context's scratch.  Sample, splitter and ordered-key arrays hold keys in order
+ * form: uint32_t for AMS_U32 / AMS_F32 (float keys mapped as described above) and
+ * uint64_t for AMS_U64. */
+
+/* Section 6, "random sample of size abr": d_sample[j] = key[idx_j] (ordered form) for
+ * j < count, idx_j = floor(u_j * n / 2^64) where u_j is output j of SplitMix64 started
+ * at mix(mix(seed + (level+1)*g) + (begin+1)*g), g the SplitMix64 increment. */
+AMS_API ams_status ams_step_sample(const void* d_keys, uint64_t n, ams_key_type kt, uint32_t count,
+                           uint64_t seed, uint32_t level, uint64_t begin, void* d_sample,
+                           void* stream);
+
+/* Section 4.2, fast work-inefficient sorting: d_sorted[rank_i] = d_sample[i] with
+ * rank_i = #{j : s_j < s_i} + #{j < i : s_j == s_i}.  count <= 65536. */
+AMS_API ams_status ams_step_rank_sort(const void* d_sample, uint32_t count, ams_key_type kt,
+                              void* d_sorted, void* stream);
+
+/* Section 6, splitters of equidistant rank: d_splitters[i] = d_sorted[(i+1)*a] for
+ * i < nbuckets-1; requires count == a*nbuckets. */
+AMS_API ams_status ams_step_splitters(const void* d_sorted, uint32_t a, uint32_t nbuckets,
+                              ams_key_type kt, void* d_splitters, void* stream);
+
+/* Section 6 partitioning with Appendix D equality buckets: for every key, j =
+ * #{splitters < key}; id = 2j, or 2j+1 if j < nbuckets-1 and key == splitter j.
+ * d_counts (2*nbuckets-1 entries, uint32) receives the bucket sizes; d_ids (n entries,
+ * uint16) the ids if not NULL.  d_splitters: nbuckets-1 sorted keys (ordered form). */
+AMS_API ams_status ams_step_classify(const void* d_keys, uint64_t n, ams_key_type kt,
+                             const void* d_splitters, uint32_t nbuckets, uint32_t* d_counts,
+                             uint16_t* d_ids, void* stream);
+
+/* Section 6 bucket grouping / Appendix C: d_L = smallest bound L for which scanning the
+ * range-bucket sizes (d_counts[0], d_counts[2], ...) forms at most r groups;
+ * d_group_ends (r entries) = exclusive end bucket of each group at that bound;
+ * d_ngroups = number of groups. */
+AMS_API ams_status ams_step_bin_pack(const uint32_t* d_counts, uint32_t nbuckets, uint32_t r,
+                             uint64_t* d_L, uint32_t* d_group_ends, uint32_t* d_ngroups,
+                             void* stream);
+
+/* Section 6 delivery: stable partition of d_in into d_out by bucket id (ids as in
+ * ams_step_classify); payloads move along when d_vals_in is not NULL. */
+AMS_API ams_status ams_step_partition(const void* d_in, void* d_out, const uint64_t* d_vals_in,
+                              uint64_t* d_vals_out, uint64_t n, ams_key_type kt,
+                              const void* d_splitters, uint32_t nbuckets, void* stream);
+
+/* Section 6 base case: stable sort of n <= basecase capacity keys (and payloads) in
+ * place in shared memory. */
+AMS_API ams_status ams_step_base_case(void* d_keys, uint64_t* d_vals, uint64_t n, ams_key_type kt,
+                              void* stream);
+
+/* --------------------------------------------------------------- misc */
+AMS_API const char* ams_status_string(ams_status s);
+/* Default base-case capacity for a key type (pairs != 0 for key-value sorts). */
+AMS_API uint32_t ams_default_basecase_cap(ams_key_type kt, int pairs);
+/* Library version, e.g. "0.1.0". */
+AMS_API const char* ams_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMS_H */

@@ -390,8 +390,11 @@ class Plan:
     def nbuckets(self, level):         # 1-based level
         return self.b * self.r[level - 1]
 
-    def a_for(self, n_g):
-        return self.a if self.a else oversampling_factor(n_g)
+    def a_for(self, n_g, nbuckets):
+        """READING: a = the fixed value or ceil(1.6 log10 n_g), but never more than
+        max(1, n_g // (16 B)), so a segment's sample stays within 1/16 of it."""
+        a = self.a if self.a else oversampling_factor(n_g)
+        return min(a, max(1, n_g // (16 * nbuckets)))
 
 
 def plan(n_max: int, kt: int, levels: int, r, pairs=False, b=None, a=None, C=None) -> Plan:
@@ -440,7 +443,7 @@ def ams_sort(kt: int, keys: np.ndarray, pl: Plan, seed: int, vals=None, offsets=
             if n_g <= pl.C:
                 leaves.append((lo, hi, 0))
                 continue
-            a = pl.a_for(n_g)
+            a = pl.a_for(n_g, B)
             S = a * B
             seg = t[lo:hi]
             smp = sample(seg, seed, level, lo, S)

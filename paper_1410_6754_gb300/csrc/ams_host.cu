@@ -1,0 +1,946 @@
+// Host side of libams: plan of the levels, scratch memory (contexts), the launch
+// sequence of one sort and the C ABI declared in include/ams.h.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "ams_internal.cuh"
+
+namespace ams {
+
+cudaError_t launch_sample_sort_ex(const LevelArgs& a, int ksize, int grid, void* raw_out,
+                                  const void* sample_in, cudaStream_t s);
+cudaError_t launch_splitters_ex(const LevelArgs& a, int ksize, int grid, void* sorted_out,
+                                cudaStream_t s);
+
+namespace {
+
+// ------------------------------------------------------------------------- plan
+struct LevelPlan {
+  uint32_t r, B, logBp, nid, CH;
+  uint64_t nseg_cap, samples_cap, items_cap, bc_cap, next_cap;
+};
+
+struct Plan {
+  int L = 0;
+  uint32_t b = 0, a_fixed = 0, C = 0;
+  int ksize = 8;
+  bool pairs = false;
+  uint64_t n = 0, nseg_user = 1;
+  uint64_t seg1_cap = 0, bc0_cap = 0;
+  LevelPlan lv[kMaxLevels];
+};
+
+uint32_t default_cap(ams_key_type kt, bool pairs) {
+  if (pairs) return 8192;
+  return (kt == AMS_U32 || kt == AMS_F32) ? 16384u : 8192u;
+}
+
+int ksize_of(ams_key_type kt) { return kt == AMS_U64 ? 8 : 4; }
+
+ams_status make_plan(uint64_t n, uint64_t nseg_user, ams_key_type kt, bool pairs, int levels,
+                     const uint32_t* r, const ams_options* opt, int sm_count, Plan* p) {
+  if (levels < 1 || levels > kMaxLevels || r == nullptr) return AMS_ERR_INVALID;
+  if (kt != AMS_U32 && kt != AMS_U64 && kt != AMS_F32) return AMS_ERR_INVALID;
+  ams_options o{};
+  if (opt) o = *opt;
+  p->ksize = ksize_of(kt);
+  p->pairs = pairs;
+  p->n = n;
+  p->nseg_user = nseg_user;
+  p->b = o.overpartition_b ? o.overpartition_b : (levels == 1 ? 1u : 4u);
+  p->a_fixed = o.oversample_a;
+  if (p->a_fixed > 64) return AMS_ERR_INVALID;
+  const uint32_t maxcap = basecase_max_cap(p->ksize, pairs);
+  p->C = o.basecase_cap ? o.basecase_cap : default_cap(kt, pairs);
+  if (p->C > maxcap) return AMS_ERR_UNSUPPORTED;
+  std::vector<uint32_t> rr(r, r + levels);
+  for (uint32_t x : rr)
+    if (x < 2) return AMS_ERR_INVALID;
+  uint64_t est = n;
+  for (uint32_t x : rr) est = (est + x - 1) / x;
+  while (est > p->C && (int)rr.size() < kMaxLevels) {
+    rr.push_back(rr.back());
+    est = (est + rr.back() - 1) / rr.back();
+  }
+  p->L = (int)rr.size();
+  const uint64_t C = p->C;
+  const uint64_t big = n / (C + 1) + 1;  // segments larger than C that fit in n
+  p->seg1_cap = std::min<uint64_t>(nseg_user, big);
+  p->bc0_cap = std::min<uint64_t>(nseg_user, n) + 1;
+  uint64_t nseg_cap = p->seg1_cap;
+  const uint64_t chunk_goal = (n + (uint64_t)sm_count * 8 - 1) / ((uint64_t)sm_count * 8);
+  for (int l = 0; l < p->L; ++l) {
+    LevelPlan& lp = p->lv[l];
+    lp.r = rr[l];
+    const uint64_t B = (uint64_t)p->b * rr[l];
+    if (B < 2 || B > (uint64_t)kMaxBuckets) return AMS_ERR_UNSUPPORTED;
+    lp.B = (uint32_t)B;
+    lp.logBp = 0;
+    while ((1u << lp.logBp) < lp.B) ++lp.logBp;
+    lp.nid = 2 * lp.B - 1;
+    lp.CH = (uint32_t)std::max<uint64_t>(8192, (chunk_goal + 8191) / 8192 * 8192);
+    lp.nseg_cap = std::max<uint64_t>(nseg_cap, 1);
+    lp.samples_cap = lp.nseg_cap * B + n / 16 + 1;
+    lp.items_cap = n / lp.CH + lp.nseg_cap + 1;
+    lp.bc_cap = 5 * (n / C + 1) + lp.nseg_cap * lp.r + n / kCopyChunk + 16;
+    lp.next_cap = std::min<uint64_t>(lp.nseg_cap * (2 * B - 1), big);
+    nseg_cap = lp.next_cap;
+  }
+  return AMS_OK;
+}
+
+// -------------------------------------------------------------------- workspace
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <typename T>
+  T* take(uint64_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off += (size_t)count * sizeof(T);
+    return p;
+  }
+};
+
+struct LevelBufs {
+  Seg* segs_next;
+  SegInfo* sinfo;
+  void* sample;
+  uint32_t* srank;
+  void* spl;
+  uint32_t* counts;
+  uint32_t* totals;
+  uint32_t* seg_L;
+  uint32_t* seg_ng;
+  BcItem* bc;
+};
+
+struct Bufs {
+  void* tmp;
+  uint64_t* vtmp;
+  LevelCounters* ctr;  // L + 1 entries: [0] = init, [l] = level l
+  uint32_t* status;
+  Seg* segs1;
+  BcItem* bc0;
+  LevelBufs lv[kMaxLevels];
+};
+
+size_t carve(const Plan& p, char* base, Bufs* b) {
+  Carver c{base};
+  b->status = c.take<uint32_t>(64);
+  b->ctr = c.take<LevelCounters>(kMaxLevels + 1);
+  b->tmp = c.take<char>(p.n * p.ksize);
+  b->vtmp = p.pairs ? c.take<uint64_t>(p.n) : nullptr;
+  b->segs1 = c.take<Seg>(p.seg1_cap + 1);
+  b->bc0 = c.take<BcItem>(p.bc0_cap);
+  for (int l = 0; l < p.L; ++l) {
+    const LevelPlan& lp = p.lv[l];
+    LevelBufs& lb = b->lv[l];
+    lb.sinfo = c.take<SegInfo>(lp.nseg_cap);
+    lb.sample = c.take<char>(lp.samples_cap * p.ksize);
+    lb.srank = c.take<uint32_t>(lp.samples_cap);
+    lb.spl = c.take<char>(lp.nseg_cap * (lp.B - 1) * p.ksize);
+    lb.counts = c.take<uint32_t>(lp.items_cap * lp.nid);
+    lb.totals = c.take<uint32_t>(lp.nseg_cap * lp.nid);
+    lb.seg_L = c.take<uint32_t>(lp.nseg_cap);
+    lb.seg_ng = c.take<uint32_t>(lp.nseg_cap);
+    lb.bc = c.take<BcItem>(lp.bc_cap);
+    lb.segs_next = c.take<Seg>(lp.next_cap + 1);
+  }
+  return c.off + 256;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------- context
+struct Context {
+  int device = 0;
+  uint64_t budget = 0;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  uint32_t* d_status = nullptr;  // lives at the start of ws
+  cudaStream_t last_stream = nullptr;
+  bool has_run = false;
+  int sm_count = 148;
+  // statistics of the last sort
+  Plan last_plan;
+  Bufs last_bufs{};
+  uint32_t launches = 0;
+  bool timers = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_kind;
+  size_t ev_used = 0;
+  uint64_t kind_elems[AMS_K_COUNT] = {};
+  // host-buffer calls
+  char* stage = nullptr;
+  size_t stage_bytes = 0;
+  // step calls
+  char* step_ws = nullptr;
+  size_t step_bytes = 0;
+  std::mutex mu;
+};
+
+static ams_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return AMS_OK;
+  if (e == cudaErrorMemoryAllocation) return AMS_ERR_OOM;
+  return AMS_ERR_CUDA;
+}
+
+#define AMS_TRY(expr)                           \
+  do {                                          \
+    cudaError_t _e = (expr);                    \
+    if (_e != cudaSuccess) return cuda_status(_e); \
+  } while (0)
+
+static ams_status grow(Context* cx, char** buf, size_t* have, size_t need) {
+  if (*have >= need) return AMS_OK;
+  const size_t total = cx->ws_bytes + cx->stage_bytes + cx->step_bytes - *have + need;
+  if (cx->budget && total > cx->budget) return AMS_ERR_OOM;
+  if (*buf) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_status(e);
+    cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, need);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return AMS_ERR_OOM;
+  }
+  *buf = (char*)p;
+  *have = need;
+  return AMS_OK;
+}
+
+static ams_status ensure_ws(Context* cx, size_t need) {
+  const bool fresh = cx->ws == nullptr || cx->ws_bytes < need;
+  ams_status st = grow(cx, &cx->ws, &cx->ws_bytes, need);
+  if (st != AMS_OK) return st;
+  if (fresh) {
+    cx->d_status = (uint32_t*)cx->ws;
+    AMS_TRY(cudaMemset(cx->d_status, 0, 256));
+  }
+  return AMS_OK;
+}
+
+static std::mutex g_default_mu;
+static Context* g_default[64] = {};
+
+static Context* default_context() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_default_mu);
+  if (!g_default[dev]) {
+    Context* cx = new (std::nothrow) Context();
+    if (!cx) return nullptr;
+    cx->device = dev;
+    cudaDeviceGetAttribute(&cx->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    g_default[dev] = cx;
+  }
+  return g_default[dev];
+}
+
+// Kernel launch bookkeeping: count, and optional events around the launch.
+struct Launcher {
+  Context* cx;
+  cudaStream_t s;
+  int kind = 0;
+  void begin(int k) {
+    kind = k;
+    if (!cx->timers) return;
+    if (cx->ev_used + 2 > cx->ev_pool.size()) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cx->ev_pool.push_back(e);
+      }
+    }
+    cudaEventRecord(cx->ev_pool[cx->ev_used], s);
+  }
+  cudaError_t end(cudaError_t e) {
+    cx->launches++;
+    if (cx->timers) {
+      cudaEventRecord(cx->ev_pool[cx->ev_used + 1], s);
+      cx->ev_kind.push_back(kind);
+      cx->ev_used += 2;
+    }
+    return e;
+  }
+};
+
+static void fill_thr(double* thr) {
+  for (int a = 0; a < kThrCount; ++a) thr[a] = std::pow(10.0, a / 1.6);
+}
+
+// --------------------------------------------------------------- one whole sort
+static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
+  if (!rq) return AMS_ERR_INVALID;
+  const bool pairs = rq->vals_in != nullptr || rq->vals_out != nullptr;
+  if (pairs && (rq->vals_in == nullptr || rq->vals_out == nullptr)) return AMS_ERR_INVALID;
+  if (rq->n >= 0xFFFFFFFFull) return AMS_ERR_UNSUPPORTED;
+  const uint64_t nseg_user = rq->d_offsets ? rq->nseg : 1;
+  if (rq->n == 0 || nseg_user == 0) {
+    cx->has_run = false;
+    return AMS_OK;
+  }
+  if (!rq->keys_in || !rq->keys_out) return AMS_ERR_INVALID;
+  const int ks = ksize_of(rq->kt);
+  if (((uintptr_t)rq->keys_in % ks) || ((uintptr_t)rq->keys_out % ks)) return AMS_ERR_INVALID;
+  Plan p;
+  ams_status st = make_plan(rq->n, nseg_user, rq->kt, pairs, rq->levels, rq->buckets_per_level,
+                            &rq->opt, cx->sm_count, &p);
+  if (st != AMS_OK) return st;
+  Bufs b{};
+  const size_t need = carve(p, nullptr, &b);
+  if ((st = ensure_ws(cx, need)) != AMS_OK) return st;
+  carve(p, cx->ws, &b);
+
+  // launch counts and kernel events accumulate until ams_get_stats reads them
+  cx->timers = (rq->opt.flags & AMS_FLAG_PHASE_TIMERS) != 0;
+  cx->last_plan = p;
+  cx->last_bufs = b;
+  cx->last_stream = s;
+  cx->has_run = true;
+
+  const bool f32 = rq->kt == AMS_F32;
+  const bool inplace = rq->keys_in == rq->keys_out;
+  const int SM = cx->sm_count;
+  Launcher ln{cx, s};
+
+  AMS_TRY(cudaMemsetAsync(b.ctr, 0, sizeof(LevelCounters) * (kMaxLevels + 1), s));
+
+  // level 0: split the user's segments
+  InitArgs ia{};
+  ia.offsets = rq->d_offsets;
+  ia.nseg = nseg_user;
+  ia.n = (uint32_t)rq->n;
+  ia.C = p.C;
+  ia.need_copy_small = (!inplace || f32) ? 1 : 0;
+  ia.segs1 = b.segs1;
+  ia.bc0 = b.bc0;
+  ia.ctr0 = &b.ctr[0];
+  ia.status = b.status;
+  ia.seg_cap = (uint32_t)p.seg1_cap;
+  ia.bc_cap = (uint32_t)p.bc0_cap;
+  const int init_grid = (int)std::min<uint64_t>((nseg_user + 255) / 256, (uint64_t)SM * 8);
+  ln.begin(AMS_K_INIT);
+  AMS_TRY(ln.end(launch_init(ia, init_grid, s)));
+
+  const uint64_t bc_grid_cap = (uint64_t)SM * (p.ksize == 4 && !p.pairs ? 1 : 2);
+  BaseArgs ba{};
+  ba.out = rq->keys_out;
+  ba.vout = rq->vals_out;
+  auto run_basecase = [&](const void* src, const uint64_t* vsrc, const BcItem* items,
+                          const LevelCounters* ctr, int tf_load, uint64_t cap_items) -> ams_status {
+    ba.src = src;
+    ba.vsrc = vsrc;
+    ba.scratch = (src == rq->keys_out) ? b.tmp : rq->keys_out;
+    ba.vscratch = (src == rq->keys_out) ? b.vtmp : rq->vals_out;
+    ba.items = items;
+    ba.ctr = ctr;
+    ba.tf_load = tf_load;
+    ba.tf_store = f32 ? 1 : 0;
+    ba.status = b.status;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(cap_items, bc_grid_cap));
+    ln.begin(AMS_K_BASECASE);
+    cudaError_t e = ln.end(launch_basecase(ba, p.ksize, p.pairs, grid, s));
+    return cuda_status(e);
+  };
+  if ((st = run_basecase(rq->keys_in, rq->vals_in, b.bc0, &b.ctr[0], f32 ? 1 : 0, p.bc0_cap)) != AMS_OK)
+    return st;
+
+  LevelArgs la{};
+  fill_thr(la.a_thr);
+  la.seed = rq->seed;
+  la.a_fixed = p.a_fixed;
+  la.C = p.C;
+  la.status = b.status;
+  for (int l = 1; l <= p.L; ++l) {
+    const LevelPlan& lp = p.lv[l - 1];
+    const LevelBufs& lb = b.lv[l - 1];
+    la.level = l;
+    la.B = lp.B;
+    la.logBp = lp.logBp;
+    la.nid = lp.nid;
+    la.r = lp.r;
+    la.CH = lp.CH;
+    la.last = l == p.L;
+    if (l == 1) {
+      la.src = rq->keys_in;
+      la.vsrc = rq->vals_in;
+      la.dst = b.tmp;
+      la.vdst = b.vtmp;
+      la.tf_src = f32 ? 1 : 0;
+      la.segs = b.segs1;
+    } else {
+      const bool even = (l % 2) == 0;
+      la.src = even ? b.tmp : rq->keys_out;
+      la.vsrc = even ? b.vtmp : rq->vals_out;
+      la.dst = even ? rq->keys_out : b.tmp;
+      la.vdst = even ? rq->vals_out : b.vtmp;
+      la.tf_src = 0;
+      la.segs = b.lv[l - 2].segs_next;
+    }
+    la.copy_final = (la.dst != rq->keys_out || f32) ? 1 : 0;
+    la.in_ctr = &b.ctr[l - 1];
+    la.ctr = &b.ctr[l];
+    la.sinfo = lb.sinfo;
+    la.sample = lb.sample;
+    la.srank = lb.srank;
+    la.spl = lb.spl;
+    la.counts = lb.counts;
+    la.totals = lb.totals;
+    la.seg_L = lb.seg_L;
+    la.seg_ng = lb.seg_ng;
+    la.group_ends = nullptr;
+    la.segs_next = lb.segs_next;
+    la.bc = lb.bc;
+    la.nseg_cap = (uint32_t)lp.nseg_cap;
+    la.samples_cap = (uint32_t)std::min<uint64_t>(lp.samples_cap, 0xFFFFFFFFull);
+    la.items_cap = (uint32_t)std::min<uint64_t>(lp.items_cap, 0xFFFFFFFFull);
+    la.next_cap = (uint32_t)lp.next_cap;
+    la.bc_cap = (uint32_t)std::min<uint64_t>(lp.bc_cap, 0xFFFFFFFFull);
+    const int wide = SM * 4;
+    const int seg_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(lp.nseg_cap, (uint64_t)SM * 2));
+    ln.begin(AMS_K_SETUP);
+    AMS_TRY(ln.end(launch_setup(la, s)));
+    ln.begin(AMS_K_SAMPLE_SORT);
+    AMS_TRY(ln.end(launch_sample_sort(la, p.ksize, wide, s)));
+    ln.begin(AMS_K_CROSS_RANK);
+    AMS_TRY(ln.end(launch_cross_rank(la, p.ksize, wide, s)));
+    ln.begin(AMS_K_SPLITTERS);
+    AMS_TRY(ln.end(launch_splitters(la, p.ksize, wide, s)));
+    ln.begin(AMS_K_CLASSIFY);
+    AMS_TRY(ln.end(launch_classify(la, p.ksize, SM * 4, nullptr, s)));
+    ln.begin(AMS_K_SCAN);
+    AMS_TRY(ln.end(launch_scan(la, SM * 8, s)));
+    ln.begin(AMS_K_BINPACK);
+    AMS_TRY(ln.end(launch_binpack(la, seg_grid, s)));
+    ln.begin(AMS_K_SCATTER);
+    AMS_TRY(ln.end(launch_scatter(la, p.ksize, p.pairs, SM * 2, s)));
+    if ((st = run_basecase(la.dst, la.vdst, lb.bc, &b.ctr[l], 0, lp.bc_cap)) != AMS_OK) return st;
+  }
+  return AMS_OK;
+}
+
+static ams_status read_status(Context* cx) {
+  if (!cx->ws) return AMS_OK;
+  uint32_t v = 0;
+  AMS_TRY(cudaMemcpy(&v, cx->d_status, 4, cudaMemcpyDeviceToHost));
+  if (v) AMS_TRY(cudaMemset(cx->d_status, 0, 4));
+  if (v & ST_TIMEOUT) return AMS_ERR_TIMEOUT;
+  if (v & ST_OVERFLOW) return AMS_ERR_INTERNAL;
+  return AMS_OK;
+}
+
+// -------------------------------------------------------------------- step calls
+struct StepWs {
+  Seg* segs;
+  LevelCounters* ctr;  // [0] input, [1] level
+  SegInfo* sinfo;
+  void* sample;
+  uint32_t* srank;
+  void* spl;
+  uint32_t* counts;
+  uint32_t* totals;
+  uint32_t* seg_L;
+  uint32_t* seg_ng;
+  BcItem* bc;
+  Seg* segs_next;
+};
+
+__global__ void k_step_prepare(Seg* segs, LevelCounters* ctr, uint32_t begin, uint32_t end,
+                               uint32_t* srank_iota, uint32_t iota_n) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    segs[0] = Seg{begin, end};
+    ctr[0] = LevelCounters{};
+    ctr[1] = LevelCounters{};
+    ctr[0].nseg_next = 1;
+  }
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < iota_n; i += gridDim.x * blockDim.x)
+    srank_iota[i] = i;
+}
+
+__global__ void k_step_finish_binpack(const uint32_t* seg_L, const uint32_t* seg_ng, uint64_t* d_L,
+                                      uint32_t* d_ng) {
+  if (threadIdx.x == 0) {
+    if (d_L) *d_L = seg_L[0];
+    if (d_ng) *d_ng = seg_ng[0];
+  }
+}
+
+__global__ void k_step_item(BcItem* items, LevelCounters* ctr, uint32_t b, uint32_t e) {
+  if (threadIdx.x == 0) {
+    items[0] = BcItem{b, e, BC_SORT, 0};
+    *ctr = LevelCounters{};
+    ctr->n_bc = 1;
+  }
+}
+
+// Scratch for a one-segment level: up to `samples` sample keys, `B` buckets and
+// `items` chunks.
+static ams_status step_ws(Context* cx, uint64_t samples, uint32_t B, uint64_t items, int ks,
+                          StepWs* w) {
+  const uint32_t nid = 2 * B - 1;
+  auto lay = [&](char* base) {
+    Carver c{base};
+    w->segs = c.take<Seg>(2);
+    w->ctr = c.take<LevelCounters>(2);
+    w->sinfo = c.take<SegInfo>(1);
+    w->sample = c.take<char>((samples + 1) * ks);
+    w->srank = c.take<uint32_t>(samples + 1);
+    w->spl = c.take<char>((uint64_t)(B + 1) * ks);
+    w->counts = c.take<uint32_t>(items * nid);
+    w->totals = c.take<uint32_t>(nid + 1);
+    w->seg_L = c.take<uint32_t>(1);
+    w->seg_ng = c.take<uint32_t>(1);
+    w->bc = c.take<BcItem>(2 * (uint64_t)nid + 16);
+    w->segs_next = c.take<Seg>(2 * (uint64_t)nid + 16);
+    return c.off + 256;
+  };
+  const size_t need = lay(nullptr);
+  ams_status st = grow(cx, &cx->step_ws, &cx->step_bytes, need);
+  if (st != AMS_OK) return st;
+  if (cx->ws == nullptr) {
+    if ((st = ensure_ws(cx, 4096)) != AMS_OK) return st;
+  }
+  lay(cx->step_ws);
+  return AMS_OK;
+}
+
+static LevelArgs step_level(Context* cx, const StepWs& w, uint32_t B, uint32_t a_fixed, uint32_t n) {
+  LevelArgs la{};
+  fill_thr(la.a_thr);
+  la.level = 1;
+  la.B = B;
+  la.logBp = 0;
+  while ((1u << la.logBp) < B) ++la.logBp;
+  la.nid = 2 * B - 1;
+  la.r = B;
+  la.a_fixed = a_fixed;
+  la.C = 0x7FFFFFFFu;
+  la.CH = (uint32_t)std::max<uint64_t>(8192, ((uint64_t)n / (cx->sm_count * 4) + 8191) / 8192 * 8192);
+  la.last = 1;
+  la.copy_final = 0;
+  la.segs = w.segs;
+  la.in_ctr = &w.ctr[0];
+  la.ctr = &w.ctr[1];
+  la.sinfo = w.sinfo;
+  la.sample = w.sample;
+  la.srank = w.srank;
+  la.spl = w.spl;
+  la.counts = w.counts;
+  la.totals = w.totals;
+  la.seg_L = w.seg_L;
+  la.seg_ng = w.seg_ng;
+  la.segs_next = w.segs_next;
+  la.bc = w.bc;
+  la.status = cx->d_status;
+  la.nseg_cap = 1;
+  la.samples_cap = 0xFFFFFFFFu;
+  la.items_cap = 0xFFFFFFFFu;
+  la.next_cap = 2 * la.nid + 16;
+  la.bc_cap = 2 * la.nid + 16;
+  return la;
+}
+
+}  // namespace ams
+
+using namespace ams;
+
+static Context* ctx_or_default(void* ctx) {
+  return ctx ? static_cast<Context*>(ctx) : default_context();
+}
+
+static ams_status sort_common(const ams_request& rq, void* stream) {
+  Context* cx = default_context();
+  if (!cx) return AMS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(cx->mu);
+  return run_sort(cx, &rq, (cudaStream_t)stream);
+}
+
+static ams_request make_req(const void* in, void* out, const uint64_t* vin, uint64_t* vout,
+                            uint64_t n, ams_key_type kt, int levels, const uint32_t* r,
+                            uint64_t seed, const ams_options* opt) {
+  ams_request rq{};
+  rq.keys_in = in;
+  rq.keys_out = out;
+  rq.vals_in = vin;
+  rq.vals_out = vout;
+  rq.n = n;
+  rq.kt = kt;
+  rq.levels = levels;
+  rq.buckets_per_level = r;
+  rq.seed = seed;
+  if (opt) rq.opt = *opt;
+  return rq;
+}
+
+extern "C" {
+
+ams_status ams_sort_keys(void* d_keys, uint64_t n, ams_key_type kt, int levels,
+                         const uint32_t* buckets_per_level, uint64_t seed, const ams_options* opt,
+                         void* stream) {
+  return sort_common(make_req(d_keys, d_keys, nullptr, nullptr, n, kt, levels, buckets_per_level,
+                              seed, opt),
+                     stream);
+}
+
+ams_status ams_sort_pairs(void* d_keys, uint64_t* d_vals, uint64_t n, ams_key_type kt, int levels,
+                          const uint32_t* buckets_per_level, uint64_t seed, const ams_options* opt,
+                          void* stream) {
+  if (!d_vals) return AMS_ERR_INVALID;
+  return sort_common(make_req(d_keys, d_keys, d_vals, d_vals, n, kt, levels, buckets_per_level,
+                              seed, opt),
+                     stream);
+}
+
+ams_status ams_sort_segmented(void* d_keys, uint64_t* d_vals, const uint64_t* d_offsets,
+                              uint64_t nseg, uint64_t n, ams_key_type kt, int levels,
+                              const uint32_t* buckets_per_level, uint64_t seed,
+                              const ams_options* opt, void* stream) {
+  if (!d_offsets && nseg != 1) return AMS_ERR_INVALID;
+  ams_request rq = make_req(d_keys, d_keys, d_vals, d_vals, n, kt, levels, buckets_per_level,
+                            seed, opt);
+  rq.d_offsets = d_offsets;
+  rq.nseg = nseg;
+  return sort_common(rq, stream);
+}
+
+ams_status ams_sort_keys_into(const void* d_in, void* d_out, uint64_t n, ams_key_type kt, int levels,
+                              const uint32_t* buckets_per_level, uint64_t seed,
+                              const ams_options* opt, void* stream) {
+  return sort_common(make_req(d_in, d_out, nullptr, nullptr, n, kt, levels, buckets_per_level, seed,
+                              opt),
+                     stream);
+}
+
+ams_status ams_sort_pairs_into(const void* d_keys_in, void* d_keys_out, const uint64_t* d_vals_in,
+                               uint64_t* d_vals_out, uint64_t n, ams_key_type kt, int levels,
+                               const uint32_t* buckets_per_level, uint64_t seed,
+                               const ams_options* opt, void* stream) {
+  if (!d_vals_in || !d_vals_out) return AMS_ERR_INVALID;
+  return sort_common(make_req(d_keys_in, d_keys_out, d_vals_in, d_vals_out, n, kt, levels,
+                              buckets_per_level, seed, opt),
+                     stream);
+}
+
+ams_status ams_sort_host(void* h_keys, uint64_t* h_vals, uint64_t n, ams_key_type kt, int levels,
+                         const uint32_t* buckets_per_level, uint64_t seed, const ams_options* opt,
+                         void* stream) {
+  if (!h_keys && n) return AMS_ERR_INVALID;
+  if (n == 0) return AMS_OK;
+  Context* cx = default_context();
+  if (!cx) return AMS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(cx->mu);
+  const cudaStream_t s = (cudaStream_t)stream;
+  const size_t kb = (size_t)n * ksize_of(kt), vb = h_vals ? (size_t)n * 8 : 0;
+  ams_status st = grow(cx, &cx->stage, &cx->stage_bytes, kb + vb + 512);
+  if (st != AMS_OK) return st;
+  void* dk = cx->stage;
+  uint64_t* dv = h_vals ? (uint64_t*)(cx->stage + ((kb + 255) & ~(size_t)255)) : nullptr;
+  AMS_TRY(cudaMemcpyAsync(dk, h_keys, kb, cudaMemcpyHostToDevice, s));
+  if (dv) AMS_TRY(cudaMemcpyAsync(dv, h_vals, vb, cudaMemcpyHostToDevice, s));
+  ams_request rq = make_req(dk, dk, dv, dv, n, kt, levels, buckets_per_level, seed, opt);
+  if ((st = run_sort(cx, &rq, s)) != AMS_OK) return st;
+  AMS_TRY(cudaMemcpyAsync(h_keys, dk, kb, cudaMemcpyDeviceToHost, s));
+  if (dv) AMS_TRY(cudaMemcpyAsync(h_vals, dv, vb, cudaMemcpyDeviceToHost, s));
+  AMS_TRY(cudaStreamSynchronize(s));
+  return read_status(cx);
+}
+
+ams_status ams_context_create(uint64_t hbm_budget_bytes, void** ctx) {
+  if (!ctx) return AMS_ERR_INVALID;
+  Context* cx = new (std::nothrow) Context();
+  if (!cx) return AMS_ERR_OOM;
+  cudaGetDevice(&cx->device);
+  cudaDeviceGetAttribute(&cx->sm_count, cudaDevAttrMultiProcessorCount, cx->device);
+  cx->budget = hbm_budget_bytes;
+  *ctx = cx;
+  return AMS_OK;
+}
+
+ams_status ams_context_destroy(void* ctx) {
+  if (!ctx) return AMS_ERR_INVALID;
+  Context* cx = static_cast<Context*>(ctx);
+  if (cx->ws || cx->stage || cx->step_ws) cudaDeviceSynchronize();
+  if (cx->ws) cudaFree(cx->ws);
+  if (cx->stage) cudaFree(cx->stage);
+  if (cx->step_ws) cudaFree(cx->step_ws);
+  for (cudaEvent_t e : cx->ev_pool) cudaEventDestroy(e);
+  delete cx;
+  return AMS_OK;
+}
+
+ams_status ams_sort_request(void* ctx, const ams_request* req, void* stream) {
+  Context* cx = ctx_or_default(ctx);
+  if (!cx) return AMS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(cx->mu);
+  return run_sort(cx, req, (cudaStream_t)stream);
+}
+
+ams_status ams_context_sync(void* ctx) {
+  Context* cx = ctx_or_default(ctx);
+  if (!cx) return AMS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(cx->mu);
+  if (cx->has_run) AMS_TRY(cudaStreamSynchronize(cx->last_stream));
+  return read_status(cx);
+}
+
+uint64_t ams_context_scratch_bytes(void* ctx) {
+  Context* cx = ctx_or_default(ctx);
+  return cx ? (uint64_t)(cx->ws_bytes + cx->stage_bytes + cx->step_bytes) : 0;
+}
+
+ams_status ams_get_stats(void* ctx, ams_stats* out) {
+  if (!out) return AMS_ERR_INVALID;
+  Context* cx = ctx_or_default(ctx);
+  if (!cx) return AMS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(cx->mu);
+  std::memset(out, 0, sizeof(*out));
+  if (!cx->has_run) return AMS_OK;
+  AMS_TRY(cudaStreamSynchronize(cx->last_stream));
+  const Plan& p = cx->last_plan;
+  LevelCounters h[kMaxLevels + 1];
+  AMS_TRY(cudaMemcpy(h, cx->last_bufs.ctr, sizeof(h), cudaMemcpyDeviceToHost));
+  uint32_t stw = 0;
+  AMS_TRY(cudaMemcpy(&stw, cx->d_status, 4, cudaMemcpyDeviceToHost));
+  out->levels_planned = (uint32_t)p.L;
+  out->kernel_launches = cx->launches;
+  out->device_status = stw;
+  out->basecase_items[0] = h[0].n_bc;
+  uint64_t elems[AMS_K_COUNT] = {};
+  elems[AMS_K_BASECASE] += h[0].bc_keys;
+  for (int l = 1; l <= p.L; ++l) {
+    out->segments[l - 1] = h[l].nseg;
+    out->basecase_items[l] = h[l].n_bc;
+    elems[AMS_K_CLASSIFY] += h[l].keys;
+    elems[AMS_K_SCATTER] += h[l].keys;
+    elems[AMS_K_BASECASE] += h[l].bc_keys;
+    elems[AMS_K_SAMPLE_SORT] += h[l].samples;
+  }
+  for (int k = 0; k < AMS_K_COUNT; ++k) out->kernel_elems[k] = elems[k];
+  for (size_t i = 0; i < cx->ev_kind.size(); ++i) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, cx->ev_pool[2 * i], cx->ev_pool[2 * i + 1]);
+    out->kernel_ms[cx->ev_kind[i]] += ms;
+    out->kernel_calls[cx->ev_kind[i]] += 1;
+  }
+  cx->launches = 0;
+  cx->ev_used = 0;
+  cx->ev_kind.clear();
+  return AMS_OK;
+}
+
+// ------------------------------------------------------------------ step calls
+ams_status ams_step_sample(const void* d_keys, uint64_t n, ams_key_type kt, uint32_t count,
+                           uint64_t seed, uint32_t level, uint64_t begin, void* d_sample,
+                           void* stream) {
+  if (!d_keys || !d_sample || n == 0 || n >= 0xFFFFFFFFull || count == 0 || count > (1u << 20))
+    return AMS_ERR_INVALID;
+  Context* cx = default_context();
+  if (!cx) return AMS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(cx->mu);
+  const cudaStream_t s = (cudaStream_t)stream;
+  const int ks = ksize_of(kt);
+  StepWs w;
+  ams_status st = step_ws(cx, count, 2, 1, ks, &w);
+  if (st != AMS_OK) return st;
+  LevelArgs la = step_level(cx, w, count, 1, (uint32_t)n);
+  la.level = (int)level;
+  la.seed = seed;
+  la.rng_base = begin;
+  la.src = d_keys;
+  la.tf_src = kt == AMS_F32;
+  la.CH = 0x7FFFFFFFu;
+  k_step_prepare<<<1, 32, 0, s>>>(w.segs, w.ctr, 0, (uint32_t)n, w.srank, 0);
+  AMS_TRY(cudaGetLastError());
+  AMS_TRY(launch_setup(la, s));
+  AMS_TRY(launch_sample_sort_ex(la, ks, cx->sm_count * 2, d_sample, nullptr, s));
+  return AMS_OK;
+}
+
+ams_status ams_step_rank_sort(const void* d_sample, uint32_t count, ams_key_type kt, void* d_sorted,
+                              void* stream) {
+  if (!d_sample || !d_sorted || count == 0 || count > 65536) return AMS_ERR_INVALID;
+  Context* cx = default_context();
+  if (!cx) return AMS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(cx->mu);
+  const cudaStream_t s = (cudaStream_t)stream;
+  const int ks = ksize_of(kt);
+  StepWs w;
+  ams_status st = step_ws(cx, count, count, 1, ks, &w);
+  if (st != AMS_OK) return st;
+  LevelArgs la = step_level(cx, w, count, 1, 1);
+  la.CH = 0x7FFFFFFFu;
+  k_step_prepare<<<1, 32, 0, s>>>(w.segs, w.ctr, 0, 1, w.srank, 0);
+  AMS_TRY(cudaGetLastError());
+  AMS_TRY(launch_setup(la, s));
+  AMS_TRY(launch_sample_sort_ex(la, ks, cx->sm_count * 2, nullptr, d_sample, s));
+  AMS_TRY(launch_cross_rank(la, ks, cx->sm_count * 4, s));
+  AMS_TRY(launch_splitters_ex(la, ks, cx->sm_count * 2, d_sorted, s));
+  return AMS_OK;
+}
+
+ams_status ams_step_splitters(const void* d_sorted, uint32_t a, uint32_t nbuckets, ams_key_type kt,
+                              void* d_splitters, void* stream) {
+  if (!d_sorted || !d_splitters || a == 0 || a > 64 || nbuckets < 2 || nbuckets > 65536)
+    return AMS_ERR_INVALID;
+  Context* cx = default_context();
+  if (!cx) return AMS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(cx->mu);
+  const cudaStream_t s = (cudaStream_t)stream;
+  const int ks = ksize_of(kt);
+  const uint64_t S = (uint64_t)a * nbuckets;
+  StepWs w;
+  ams_status st = step_ws(cx, S, 2, 1, ks, &w);
+  if (st != AMS_OK) return st;
+  LevelArgs la = step_level(cx, w, nbuckets, a, 1);
+  la.CH = 0x7FFFFFFFu;
+  la.sample = const_cast<void*>(d_sorted);
+  la.spl = d_splitters;
+  // a fake segment long enough that the sample-size cap keeps a
+  const uint64_t fake = std::min<uint64_t>(16ull * a * nbuckets * 16, 0xFFFFFFF0ull);
+  k_step_prepare<<<64, 256, 0, s>>>(w.segs, w.ctr, 0, (uint32_t)fake, w.srank, (uint32_t)S);
+  AMS_TRY(cudaGetLastError());
+  AMS_TRY(launch_setup(la, s));
+  AMS_TRY(launch_splitters_ex(la, ks, cx->sm_count * 2, nullptr, s));
+  return AMS_OK;
+}
+
+ams_status ams_step_classify(const void* d_keys, uint64_t n, ams_key_type kt, const void* d_splitters,
+                             uint32_t nbuckets, uint32_t* d_counts, uint16_t* d_ids, void* stream) {
+  if (!d_keys || !d_splitters || !d_counts || n == 0 || n >= 0xFFFFFFFFull || nbuckets < 2 ||
+      nbuckets > (uint32_t)kMaxBuckets)
+    return AMS_ERR_INVALID;
+  Context* cx = default_context();
+  if (!cx) return AMS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(cx->mu);
+  const cudaStream_t s = (cudaStream_t)stream;
+  const int ks = ksize_of(kt);
+  StepWs w;
+  const uint64_t items = n / 8192 + 2;
+  ams_status st = step_ws(cx, 1, nbuckets, items, ks, &w);
+  if (st != AMS_OK) return st;
+  LevelArgs la = step_level(cx, w, nbuckets, 1, (uint32_t)n);
+  la.src = d_keys;
+  la.tf_src = kt == AMS_F32;
+  la.spl = const_cast<void*>(d_splitters);
+  la.items_cap = (uint32_t)items;
+  k_step_prepare<<<1, 32, 0, s>>>(w.segs, w.ctr, 0, (uint32_t)n, w.srank, 0);
+  AMS_TRY(cudaGetLastError());
+  AMS_TRY(launch_setup(la, s));
+  AMS_TRY(launch_classify(la, ks, cx->sm_count * 4, d_ids, s));
+  AMS_TRY(launch_scan(la, cx->sm_count * 8, s));
+  AMS_TRY(cudaMemcpyAsync(d_counts, w.totals, (size_t)la.nid * 4, cudaMemcpyDeviceToDevice, s));
+  return AMS_OK;
+}
+
+ams_status ams_step_bin_pack(const uint32_t* d_counts, uint32_t nbuckets, uint32_t r, uint64_t* d_L,
+                             uint32_t* d_group_ends, uint32_t* d_ngroups, void* stream) {
+  if (!d_counts || nbuckets < 2 || nbuckets > (uint32_t)kMaxBuckets || r == 0 || r > nbuckets)
+    return AMS_ERR_INVALID;
+  Context* cx = default_context();
+  if (!cx) return AMS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(cx->mu);
+  const cudaStream_t s = (cudaStream_t)stream;
+  StepWs w;
+  ams_status st = step_ws(cx, 1, nbuckets, 1, 8, &w);
+  if (st != AMS_OK) return st;
+  LevelArgs la = step_level(cx, w, nbuckets, 1, 1);
+  la.r = r;
+  la.group_ends = d_group_ends;
+  k_step_prepare<<<1, 32, 0, s>>>(w.segs, w.ctr, 0, 0x7FFFFFFFu, w.srank, 0);
+  AMS_TRY(cudaGetLastError());
+  AMS_TRY(launch_setup(la, s));
+  AMS_TRY(cudaMemcpyAsync(w.totals, d_counts, (size_t)la.nid * 4, cudaMemcpyDeviceToDevice, s));
+  AMS_TRY(launch_binpack(la, 1, s));
+  k_step_finish_binpack<<<1, 32, 0, s>>>(w.seg_L, w.seg_ng, d_L, d_ngroups);
+  AMS_TRY(cudaGetLastError());
+  return AMS_OK;
+}
+
+ams_status ams_step_partition(const void* d_in, void* d_out, const uint64_t* d_vals_in,
+                              uint64_t* d_vals_out, uint64_t n, ams_key_type kt,
+                              const void* d_splitters, uint32_t nbuckets, void* stream) {
+  if (!d_in || !d_out || d_in == d_out || !d_splitters || n == 0 || n >= 0xFFFFFFFFull ||
+      nbuckets < 2 || nbuckets > (uint32_t)kMaxBuckets || ((d_vals_in == nullptr) != (d_vals_out == nullptr)))
+    return AMS_ERR_INVALID;
+  Context* cx = default_context();
+  if (!cx) return AMS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(cx->mu);
+  const cudaStream_t s = (cudaStream_t)stream;
+  const int ks = ksize_of(kt);
+  StepWs w;
+  const uint64_t items = n / 8192 + 2;
+  ams_status st = step_ws(cx, 1, nbuckets, items, ks, &w);
+  if (st != AMS_OK) return st;
+  LevelArgs la = step_level(cx, w, nbuckets, 1, (uint32_t)n);
+  la.src = d_in;
+  la.dst = d_out;
+  la.vsrc = d_vals_in;
+  la.vdst = d_vals_out;
+  la.tf_src = kt == AMS_F32;
+  la.spl = const_cast<void*>(d_splitters);
+  la.items_cap = (uint32_t)items;
+  k_step_prepare<<<1, 32, 0, s>>>(w.segs, w.ctr, 0, (uint32_t)n, w.srank, 0);
+  AMS_TRY(cudaGetLastError());
+  AMS_TRY(launch_setup(la, s));
+  AMS_TRY(launch_classify(la, ks, cx->sm_count * 4, nullptr, s));
+  AMS_TRY(launch_scan(la, cx->sm_count * 8, s));
+  AMS_TRY(launch_binpack(la, 1, s));
+  AMS_TRY(launch_scatter(la, ks, d_vals_in != nullptr, cx->sm_count * 2, s));
+  return AMS_OK;
+}
+
+ams_status ams_step_base_case(void* d_keys, uint64_t* d_vals, uint64_t n, ams_key_type kt, void* stream) {
+  const int ks = ksize_of(kt);
+  if (!d_keys || n == 0 || n > basecase_max_cap(ks, d_vals != nullptr)) return AMS_ERR_INVALID;
+  Context* cx = default_context();
+  if (!cx) return AMS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(cx->mu);
+  const cudaStream_t s = (cudaStream_t)stream;
+  StepWs w;
+  ams_status st = step_ws(cx, 1, 2, 1, ks, &w);
+  if (st != AMS_OK) return st;
+  k_step_item<<<1, 32, 0, s>>>(w.bc, &w.ctr[1], 0, (uint32_t)n);
+  AMS_TRY(cudaGetLastError());
+  BaseArgs ba{};
+  ba.src = d_keys;
+  ba.out = d_keys;
+  ba.scratch = nullptr;
+  ba.vsrc = d_vals;
+  ba.vout = d_vals;
+  ba.items = w.bc;
+  ba.ctr = &w.ctr[1];
+  ba.tf_load = kt == AMS_F32;
+  ba.tf_store = kt == AMS_F32;
+  ba.status = cx->d_status;
+  AMS_TRY(launch_basecase(ba, ks, d_vals != nullptr, 1, s));
+  return AMS_OK;
+}
+
+const char* ams_status_string(ams_status s) {
+  switch (s) {
+    case AMS_OK: return "ok";
+    case AMS_ERR_INVALID: return "invalid argument";
+    case AMS_ERR_OOM: return "out of device memory";
+    case AMS_ERR_CUDA: return "CUDA runtime error";
+    case AMS_ERR_TIMEOUT: return "device wait timed out";
+    case AMS_ERR_UNSUPPORTED: return "unsupported request";
+    case AMS_ERR_INTERNAL: return "device table overflow";
+  }
+  return "unknown status";
+}
+
+uint32_t ams_default_basecase_cap(ams_key_type kt, int pairs) { return default_cap(kt, pairs != 0); }
+
+const char* ams_version(void) { return "0.1.0"; }
+
+}  // extern "C"

@@ -1,0 +1,254 @@
+// Bucket grouping and the next level's work tables (Section 6 with Appendix C), and
+// the level-0 split of the user's segments.
+//
+// binpack (one block per segment):
+//   * exclusive scan of the 2B-1 bucket sizes -> bucket starts (relative to the
+//     segment), overwriting the totals table;
+//   * the optimal bound L* of the scanning algorithm over the range-bucket sizes
+//     (equality buckets weigh 0: they are final).  Search of Appendix C: each round
+//     32 warps scan 32 bounds spread over [lo, hi); a successful scan lowers hi to
+//     the largest group it formed, a failed one raises lo to the smallest
+//     "group + next bucket" load it saw; the answer is lo == hi.  One warp scans
+//     one bound: a group starting at bucket s ends at the largest e with
+//     P[e] - P[s] <= L, found 32 buckets at a time by a ballot;
+//   * the groups at L*, then the pieces of every group (one thread per group):
+//     equality buckets holding at least max(2, L*/16) keys become final pieces,
+//     the rest of the group stays one piece; pieces larger than C go to the next
+//     level (or to the global-memory fallback on the last level), smaller ones are
+//     packed into base-case items of at most C keys.
+#include "cta_utils.cuh"
+
+namespace ams {
+
+struct ScanResult {
+  uint32_t groups;  // groups formed (stops counting past r)
+  uint32_t used;    // largest group formed
+  uint64_t zmin;    // smallest (group + next bucket) seen when closing a group
+};
+
+// Scanning algorithm with bound L over prefix sums P[0..B] (P[0] = 0), by one warp.
+__device__ ScanResult warp_scan_groups(const uint32_t* P, uint32_t B, uint32_t r, uint64_t L,
+                                       uint32_t* ends) {
+  const uint32_t lane = threadIdx.x & 31;
+  ScanResult res{0, 0, ~0ull};
+  uint32_t s = 0;
+  while (s < B) {
+    if (res.groups == r) {  // one group too many: infeasible
+      res.groups = r + 1;
+      break;
+    }
+    ++res.groups;
+    const uint32_t base = P[s];
+    uint32_t fit = 0;
+    for (uint32_t off = s + 1;; off += 32) {
+      const uint32_t e = off + lane;
+      const bool ok = e <= B && (uint64_t)(P[e] - base) <= L;
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, ok);
+      const uint32_t c = __popc(m);
+      fit += c;
+      if (c < 32) break;
+    }
+    const uint32_t e = s + fit;  // >= s+1 because every bucket fits alone
+    const uint32_t load = P[e] - base;
+    res.used = max(res.used, load);
+    if (e < B) res.zmin = min(res.zmin, (uint64_t)(P[e + 1] - base));
+    if (ends && lane == 0) ends[res.groups - 1] = e;
+    s = e;
+  }
+  return res;
+}
+
+struct Emitter {
+  const LevelArgs* a;
+  uint32_t seg_begin;
+  uint32_t cur_b, cur_e;  // open base-case item (relative positions), empty if equal
+
+  __device__ void push_bc(uint32_t b, uint32_t e, uint32_t kind) {
+    const uint32_t i = atomicAdd(&a->ctr->n_bc, 1u);
+    atomicAdd(&a->ctr->bc_keys, e - b);
+    if (i < a->bc_cap) {
+      a->bc[i] = BcItem{seg_begin + b, seg_begin + e, kind, 0};
+    } else {
+      atomicOr(a->status, ST_OVERFLOW);
+    }
+  }
+  __device__ void flush() {
+    if (cur_e > cur_b) push_bc(cur_b, cur_e, BC_SORT);
+    cur_b = cur_e = 0;
+  }
+  __device__ void leaf(uint32_t b, uint32_t e) {
+    if (cur_e > cur_b && cur_e == b && e - cur_b <= a->C) {
+      cur_e = e;
+    } else {
+      flush();
+      cur_b = b;
+      cur_e = e;
+    }
+  }
+  __device__ void piece(uint32_t b, uint32_t e, bool fin) {
+    const uint32_t m = e - b;
+    if (m == 0) return;
+    if (m <= a->C) {
+      leaf(b, e);
+      return;
+    }
+    flush();
+    if (fin) {
+      if (a->copy_final)
+        for (uint32_t c = b; c < e; c += kCopyChunk) push_bc(c, min(e, c + kCopyChunk), BC_COPY);
+      return;
+    }
+    if (!a->last) {
+      const uint32_t i = atomicAdd(&a->ctr->nseg_next, 1u);
+      if (i < a->next_cap) {
+        a->segs_next[i] = Seg{seg_begin + b, seg_begin + e};
+      } else {
+        atomicOr(a->status, ST_OVERFLOW);
+      }
+    } else {
+      push_bc(b, e, BC_BIG);
+    }
+  }
+};
+
+__global__ void __launch_bounds__(1024) k_binpack(LevelArgs a) {
+  constexpr int NT = 1024;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint32_t nid = a.nid, B = a.B;
+  uint32_t* cnt_s = (uint32_t*)smem;   // nid
+  uint32_t* bst_s = cnt_s + nid;       // nid + 1
+  uint32_t* P = bst_s + nid + 1;       // B + 1
+  uint32_t* ends = P + B + 1;          // r
+  __shared__ uint32_t ws[33];
+  __shared__ unsigned long long lohi[2];
+  __shared__ ScanResult wres[32];
+  __shared__ uint32_t ngroups_s;
+  const uint32_t nseg = a.ctr->nseg;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+
+  for (uint32_t g = blockIdx.x; g < nseg; g += gridDim.x) {
+    const Seg sg = a.segs[g];
+    uint32_t* tot = a.totals + (size_t)g * nid;
+    for (uint32_t i = tid; i < nid; i += NT) cnt_s[i] = bst_s[i] = tot[i];
+    __syncthreads();
+    const uint32_t n_g = block_scan_array<NT, uint32_t>(bst_s, nid, ws);
+    if (tid == 0) bst_s[nid] = n_g;
+    for (uint32_t i = tid; i < nid; i += NT) tot[i] = bst_s[i];
+    for (uint32_t j = tid; j < B; j += NT) P[j] = cnt_s[2 * j];
+    __syncthreads();
+    // max range bucket, then prefix sums of the range buckets
+    uint32_t mw = 0;
+    for (uint32_t j = tid; j < B; j += NT) mw = max(mw, P[j]);
+    const uint32_t max_w = block_reduce_max<NT, uint32_t>(mw, ws);
+    const uint32_t W = block_scan_array<NT, uint32_t>(P, B, ws);
+    if (tid == 0) {
+      P[B] = W;
+      const uint64_t lo = max((uint64_t)((W + (uint64_t)a.r - 1) / a.r), (uint64_t)max_w);
+      lohi[0] = lo;
+      lohi[1] = min((uint64_t)W, lo + max_w);
+    }
+    __syncthreads();
+    // optimal bound (Section 6 Lemma; Appendix C search).  Every round moves lo up
+    // or hi down; 64 rounds cannot be exhausted on valid input (the range starts
+    // below 2^32 and shrinks at least 32-fold per round).  The cap only guards
+    // against a logic error: it keeps the feasible hi and flags the status word.
+    for (int round = 0;; ++round) {
+      const uint64_t lo = lohi[0], hi = lohi[1];
+      if (lo >= hi) break;
+      if (round == 64) {
+        __syncthreads();
+        if (tid == 0) {
+          lohi[0] = hi;
+          atomicOr(a.status, ST_OVERFLOW);
+        }
+        __syncthreads();
+        break;
+      }
+      const uint64_t cand = lo + (hi - lo) * w / 32;
+      const ScanResult rs = warp_scan_groups(P, B, a.r, cand, nullptr);
+      if (lane == 0) wres[w] = rs;
+      __syncthreads();
+      if (tid == 0) {
+        uint64_t nlo = lo, nhi = hi;
+        for (int k = 0; k < 32; ++k) {
+          if (wres[k].groups <= a.r) nhi = min(nhi, (uint64_t)wres[k].used);
+          else nlo = max(nlo, wres[k].zmin);
+        }
+        lohi[0] = nlo;
+        lohi[1] = max(nlo, nhi);
+      }
+      __syncthreads();
+    }
+    const uint64_t Lstar = lohi[0];
+    if (w == 0) {
+      const ScanResult rs = warp_scan_groups(P, B, a.r, Lstar, ends);
+      if (lane == 0) ngroups_s = rs.groups;
+    }
+    __syncthreads();
+    const uint32_t ng = ngroups_s;
+    if (tid == 0) {
+      a.seg_L[g] = (uint32_t)Lstar;
+      a.seg_ng[g] = ng;
+    }
+    if (a.group_ends)
+      for (uint32_t i = tid; i < a.r; i += NT) a.group_ends[(size_t)g * a.r + i] = i < ng ? ends[i] : B;
+    // pieces of every group
+    const uint32_t tau = max(2u, (uint32_t)(Lstar >> 4));
+    for (uint32_t k = tid; k < ng; k += NT) {
+      Emitter em{&a, sg.begin, 0, 0};
+      const uint32_t gs = k ? ends[k - 1] : 0, ge = ends[k];
+      const uint32_t id_lo = 2 * gs, id_hi = min(2 * ge, nid);
+      uint32_t run = bst_s[id_lo];
+      for (uint32_t i = id_lo | 1; i < id_hi; i += 2) {
+        if (cnt_s[i] >= tau) {
+          em.piece(run, bst_s[i], false);
+          em.piece(bst_s[i], bst_s[i + 1], true);
+          run = bst_s[i + 1];
+        }
+      }
+      em.piece(run, bst_s[id_hi], false);
+      em.flush();
+    }
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------------------------------- init
+// User segments larger than C become level-1 segments; the others are base-case
+// items (a single key needs work only when it must be copied or untransformed).
+__global__ void __launch_bounds__(256) k_init(InitArgs a) {
+  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < a.nseg;
+       s += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t b = a.offsets ? (uint32_t)a.offsets[s] : 0u;
+    const uint32_t e = a.offsets ? (uint32_t)a.offsets[s + 1] : a.n;
+    if (e <= b) continue;
+    const uint32_t m = e - b;
+    if (m > a.C) {
+      const uint32_t i = atomicAdd(&a.ctr0->nseg_next, 1u);
+      if (i < a.seg_cap) a.segs1[i] = Seg{b, e};
+      else atomicOr(a.status, ST_OVERFLOW);
+    } else if (m > 1 || a.need_copy_small) {
+      const uint32_t i = atomicAdd(&a.ctr0->n_bc, 1u);
+      atomicAdd(&a.ctr0->bc_keys, m);
+      if (i < a.bc_cap) a.bc0[i] = BcItem{b, e, BC_SORT, 0};
+      else atomicOr(a.status, ST_OVERFLOW);
+    }
+  }
+}
+
+cudaError_t launch_init(const InitArgs& a, int grid, cudaStream_t s) {
+  k_init<<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_binpack(const LevelArgs& a, int grid, cudaStream_t s) {
+  const size_t sm = (size_t)(a.nid + a.nid + 1 + a.B + 1 + a.r) * 4;
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_binpack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  k_binpack<<<grid, 1024, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace ams

@@ -1,0 +1,68 @@
+"""The C ABI library builds, loads and exports every function include/ams.h declares
+(host-only calls; no GPU needed)."""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+import paper_1410_6754_gb300 as ams
+from paper_1410_6754_gb300 import build as B
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return B.build()
+
+
+def test_header_declares_the_boundary():
+    syms = ams.header_symbols()
+    for name in ["ams_sort_keys", "ams_sort_pairs", "ams_sort_segmented", "ams_sort_keys_into",
+                 "ams_sort_pairs_into", "ams_sort_host", "ams_context_create",
+                 "ams_context_destroy", "ams_sort_request", "ams_context_sync", "ams_get_stats",
+                 "ams_step_sample", "ams_step_rank_sort", "ams_step_splitters",
+                 "ams_step_classify", "ams_step_bin_pack", "ams_step_partition",
+                 "ams_step_base_case", "ams_status_string", "ams_version"]:
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+    missing = [s for s in ams.header_symbols() if s not in exported]
+    assert not missing, missing
+    # nothing else is exported under the ams_ prefix by accident
+    extra = sorted(s for s in exported if s.startswith("ams_") and s not in ams.header_symbols())
+    assert not extra, extra
+
+
+def test_python_binding_covers_header(libpath):
+    assert set(ams.header_symbols()) <= set(ams._SIGS)
+    L = ams.lib()
+    for name in ams.header_symbols():
+        assert hasattr(L, name)
+
+
+def test_host_only_calls(libpath):
+    L = ams.lib()
+    assert L.ams_version().decode().count(".") == 2
+    for st in range(7):
+        assert L.ams_status_string(st)
+    assert L.ams_status_string(99) == b"unknown status"
+    assert ams.default_basecase_cap(ams.U32) == 16384
+    assert ams.default_basecase_cap(ams.U64) == 8192
+    assert ams.default_basecase_cap(ams.F32, pairs=True) == 8192
+
+
+def test_struct_layouts_match_header(libpath):
+    # ams_options is 4 uint32; ams_stats layout as declared
+    assert ctypes.sizeof(ams.Options) == 16
+    assert ams.Stats.kernel_ms.offset == 4 + 4 + 32 + 36 + 4 + 4
+    assert ctypes.sizeof(ams.Request) == 8 * 7 + 4 + 4 + 8 + 8 + 16
+
+
+def test_built_for_sm103a(libpath):
+    # the fat binary carries sm_103a code (cuobjdump is not used; the build flags are checked)
+    assert "arch=compute_103a,code=sm_103a" in " ".join(B.ARCH)
+    assert os.path.getsize(libpath) > 100_000

@@ -339,7 +339,7 @@ def test_extra_levels_planned():
     pl = O.plan(1 << 28, O.KT_U64, 2, [256, 256])
     assert pl.r == [256, 256] and pl.b == 4
     pl = O.plan(1 << 20, O.KT_U32, 1, [256], b=1, a=16)
-    assert pl.r == [256] and pl.b == 1 and pl.a_for(1 << 20) == 16
+    assert pl.r == [256] and pl.b == 1 and pl.a_for(1 << 20, 256) == 16 and pl.a_for(50000, 256) == 12
 
 
 # ----------------------------------------------------------------- Lemma lm:ams-param
