@@ -285,10 +285,7 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
   if (pairs && (rq->vals_in == nullptr || rq->vals_out == nullptr)) return AMS_ERR_INVALID;
   if (rq->n >= 0xFFFFFFFFull) return AMS_ERR_UNSUPPORTED;
   const uint64_t nseg_user = rq->d_offsets ? rq->nseg : 1;
-  if (rq->n == 0 || nseg_user == 0) {
-    cx->has_run = false;
-    return AMS_OK;
-  }
+  if (rq->n == 0 || nseg_user == 0) return AMS_OK;  // nothing to sort
   if (!rq->keys_in || !rq->keys_out) return AMS_ERR_INVALID;
   const int ks = ksize_of(rq->kt);
   if (((uintptr_t)rq->keys_in % ks) || ((uintptr_t)rq->keys_out % ks)) return AMS_ERR_INVALID;
@@ -340,8 +337,11 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
                           const LevelCounters* ctr, int tf_load, uint64_t cap_items) -> ams_status {
     ba.src = src;
     ba.vsrc = vsrc;
-    ba.scratch = (src == rq->keys_out) ? b.tmp : rq->keys_out;
-    ba.vscratch = (src == rq->keys_out) ? b.vtmp : rq->vals_out;
+    // the merge fallback ping-pongs between the output and the temporary buffer: an
+    // item sits either in the temporary buffer itself (free to overwrite once read)
+    // or in the output / input, where the temporary buffer's positions are unused
+    ba.scratch = b.tmp;
+    ba.vscratch = b.vtmp;
     ba.items = items;
     ba.ctr = ctr;
     ba.tf_load = tf_load;
@@ -704,7 +704,13 @@ ams_status ams_get_stats(void* ctx, ams_stats* out) {
   if (!cx) return AMS_ERR_CUDA;
   std::lock_guard<std::mutex> lk(cx->mu);
   std::memset(out, 0, sizeof(*out));
-  if (!cx->has_run) return AMS_OK;
+  if (!cx->has_run) {
+    out->kernel_launches = cx->launches;
+    cx->launches = 0;
+    cx->ev_used = 0;
+    cx->ev_kind.clear();
+    return AMS_OK;
+  }
   AMS_TRY(cudaStreamSynchronize(cx->last_stream));
   const Plan& p = cx->last_plan;
   LevelCounters h[kMaxLevels + 1];

@@ -242,11 +242,11 @@ cudaError_t launch_init(const InitArgs& a, int grid, cudaStream_t s) {
 }
 
 cudaError_t launch_binpack(const LevelArgs& a, int grid, cudaStream_t s) {
+  // dynamic + static shared memory may pass 48 KB even when the dynamic part alone
+  // does not, so the limit is always raised to what the launch asks for
   const size_t sm = (size_t)(a.nid + a.nid + 1 + a.B + 1 + a.r) * 4;
-  if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_binpack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = cudaFuncSetAttribute(k_binpack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
   k_binpack<<<grid, 1024, sm, s>>>(a);
   return cudaGetLastError();
 }

@@ -332,7 +332,6 @@ static size_t classify_smem_bytes(int ksize, uint32_t B) {
 
 template <typename Kern>
 static cudaError_t set_smem(Kern k, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
