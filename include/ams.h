@@ -230,6 +230,29 @@ AMS_API ams_status ams_step_partition(const void* d_in, void* d_out, const uint6
 AMS_API ams_status ams_step_base_case(void* d_keys, uint64_t* d_vals, uint64_t n, ams_key_type kt,
                               void* stream);
 
+/* --------------------------------------------------------------- allocation-free sort
+ * The paper has no counterpart to this call.  It is for callers that cannot let the
+ * library allocate device memory while they call it -- for example a latency-critical
+ * loop in which cudaMalloc / cudaFree would add their implicit device-wide
+ * synchronisation, or a plug-in whose host application owns a fixed device-memory
+ * budget.  It sorts d_keys (and d_vals if not NULL) in place, with the same result as
+ * ams_sort_keys / ams_sort_pairs, using one thread block: shared-memory sorts of runs
+ * and stable pairwise merges.
+ *  - n must not exceed AMS_NOALLOC_MAX_KEYS; larger n returns AMS_ERR_INVALID and
+ *    touches nothing.  It allocates nothing: the merge scratch is one file-scope
+ *    device array of AMS_NOALLOC_MAX_KEYS * 16 bytes (8 MiB) that every GPU which
+ *    loads the library holds until the process exits.
+ *  - The first call on each device looks up that array's device address; make the
+ *    first call on a device before any stream capture.
+ *  - All calls on a device share the array.  Calls that overlap on the GPU (two
+ *    streams, or two host threads) race and give wrong results: order them on one
+ *    stream.  The array keeps the previous call's contents; the sort writes every
+ *    scratch element before reading it, so nothing needs clearing.
+ *  - Asynchronous on `stream` like the other device calls. */
+#define AMS_NOALLOC_MAX_KEYS 524288u
+AMS_API ams_status ams_sort_small_noalloc(void* d_keys, uint64_t* d_vals, uint64_t n,
+                                          ams_key_type kt, void* stream);
+
 /* --------------------------------------------------------------- misc */
 AMS_API const char* ams_status_string(ams_status s);
 /* Default base-case capacity for a key type (pairs != 0 for key-value sorts). */

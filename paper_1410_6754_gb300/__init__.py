@@ -92,6 +92,7 @@ _SIGS = {
     "ams_step_bin_pack": (_ST, [_P, _U32, _U32, _P, _P, _P, _P]),
     "ams_step_partition": (_ST, [_P, _P, _P, _P, _U64, _I, _P, _U32, _P]),
     "ams_step_base_case": (_ST, [_P, _P, _U64, _I, _P]),
+    "ams_sort_small_noalloc": (_ST, [_P, _P, _U64, _I, _P]),
     "ams_status_string": (ctypes.c_char_p, [_ST]),
     "ams_default_basecase_cap": (_U32, [_I, _I]),
     "ams_version": (ctypes.c_char_p, []),
@@ -375,4 +376,19 @@ def step_base_case(keys, vals=None, kt=None, stream=None):
     _check(lib().ams_step_base_case(_dev(keys), _dev(vals) if vals is not None else None,
                                     keys.numel(), key_type(keys, kt), _stream(stream)),
            "ams_step_base_case")
+    return keys if vals is None else (keys, vals)
+
+
+# ------------------------------------------------------------------ allocation-free sort
+NOALLOC_MAX_KEYS = 524288
+
+
+def sort_small_noalloc(keys, vals=None, kt=None, stream=None):
+    """In-place sort of at most NOALLOC_MAX_KEYS elements that allocates no device
+    memory (for callers that cannot allow allocations at call time); its scratch is
+    a fixed 8 MiB device array inside the library, shared by all calls on a device,
+    so calls must not overlap on the GPU."""
+    _check(lib().ams_sort_small_noalloc(_dev(keys), _dev(vals) if vals is not None else None,
+                                        keys.numel(), key_type(keys, kt), _stream(stream)),
+           "ams_sort_small_noalloc")
     return keys if vals is None else (keys, vals)

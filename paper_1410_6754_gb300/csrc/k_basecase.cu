@@ -7,6 +7,8 @@
 //   BC_BIG   a group still larger than C after the last level (only under extreme
 //            skew): sort runs of the block capacity with cell_sort, then merge runs
 //            pairwise (stable merge path) between the output and a scratch buffer.
+#include <mutex>
+
 #include "cta_utils.cuh"
 
 namespace ams {
@@ -166,3 +168,97 @@ cudaError_t launch_basecase(const BaseArgs& a, int ksize, bool pairs, int grid, 
 }
 
 }  // namespace ams
+
+// ===================================================================================
+// Allocation-free sort of small arrays (ams_sort_small_noalloc).
+//
+// Some callers cannot let a library allocate device memory when they call it: a
+// latency-critical loop in which cudaMalloc / cudaFree would add their implicit
+// device-wide synchronisation, or a plug-in whose host application owns a fixed
+// device-memory budget.  For them this entry point sorts up to
+// AMS_NOALLOC_MAX_KEYS elements with one block (the base-case kernel's shared-memory
+// sort of runs followed by its stable pairwise merges) and takes the merge scratch
+// from a file-scope device array instead of from a context.  The array lives as long
+// as the library is loaded, on every GPU that loads it (8 MiB per GPU).
+// ===================================================================================
+namespace ams {
+
+constexpr uint64_t kNoallocMax = AMS_NOALLOC_MAX_KEYS;
+// keys in the first half (as 64-bit slots), payloads in the second half
+static __device__ __align__(256) uint64_t g_noalloc_scratch[2 * kNoallocMax];
+
+template <typename K, bool PAIRS>
+__global__ void __launch_bounds__(512) k_sort_noalloc(void* keys, uint64_t* vals, uint32_t n, int tf,
+                                                      uint64_t* scratch) {
+  using C = BaseCfg<K, PAIRS>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  size_t off[6];
+  base_smem_layout<K, PAIRS>(off);
+  const CellSortSmem<K> sm{(K*)(smem + off[0]), (uint16_t*)(smem + off[1]), (uint32_t*)(smem + off[2]),
+                           (K*)(smem + off[4]), (uint32_t*)(smem + off[5])};
+  uint64_t* vals_s = (uint64_t*)(smem + off[3]);
+  if (n <= C::CAP) {
+    sort_block<K, PAIRS>((const K*)keys, (K*)keys, vals, vals, 0, n, tf, tf, sm, vals_s);
+    return;
+  }
+  BaseArgs a{};
+  a.src = keys;
+  a.out = keys;
+  a.scratch = scratch;                 // keys part of the static scratch
+  a.vsrc = vals;
+  a.vout = vals;
+  a.vscratch = scratch + kNoallocMax;  // payload part
+  a.tf_load = tf;
+  a.tf_store = tf;
+  big_sort<K, PAIRS>(a, 0, n, sm, vals_s);
+}
+
+}  // namespace ams
+
+namespace {
+std::mutex g_noalloc_mu;
+uint64_t* g_noalloc_ptr[64] = {};  // device address of the scratch array, per device
+}  // namespace
+
+extern "C" AMS_API ams_status ams_sort_small_noalloc(void* d_keys, uint64_t* d_vals, uint64_t n,
+                                                     ams_key_type kt, void* stream) {
+  using namespace ams;
+  if (kt != AMS_U32 && kt != AMS_U64 && kt != AMS_F32) return AMS_ERR_INVALID;
+  if (n > kNoallocMax) return AMS_ERR_INVALID;  // larger inputs need ams_sort_keys / _pairs
+  if (n == 0) return AMS_OK;
+  if (!d_keys) return AMS_ERR_INVALID;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return AMS_ERR_CUDA;
+  uint64_t* scratch = nullptr;
+  {
+    // first call on this device: look up the array's device address (host code may
+    // not use the array's name as a device pointer)
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return AMS_ERR_CUDA;
+      g_noalloc_ptr[dev] = (uint64_t*)p;
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  const bool pairs = d_vals != nullptr;
+  const int ks = kt == AMS_U64 ? 8 : 4;
+  const int tf = kt == AMS_F32 ? 1 : 0;
+  const size_t sm = basecase_smem_bytes(ks, pairs);
+  const cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+#define AMS_LAUNCH_NOALLOC(K, P)                                                               \
+  do {                                                                                         \
+    e = cudaFuncSetAttribute(k_sort_noalloc<K, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)sm);                                                         \
+    if (e == cudaSuccess) k_sort_noalloc<K, P><<<1, 512, sm, s>>>(d_keys, d_vals, (uint32_t)n, tf, scratch); \
+  } while (0)
+  if (ks == 4) {
+    if (pairs) AMS_LAUNCH_NOALLOC(uint32_t, true); else AMS_LAUNCH_NOALLOC(uint32_t, false);
+  } else {
+    if (pairs) AMS_LAUNCH_NOALLOC(uint64_t, true); else AMS_LAUNCH_NOALLOC(uint64_t, false);
+  }
+#undef AMS_LAUNCH_NOALLOC
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return e == cudaSuccess ? AMS_OK : AMS_ERR_CUDA;
+}
