@@ -72,6 +72,9 @@ typedef struct ams_options {
 } ams_options;
 
 #define AMS_FLAG_PHASE_TIMERS 0x1u  /* record CUDA events per kernel (see ams_stats) */
+#define AMS_FLAG_TREE_CLASSIFIER 0x2u  /* classify by descending the implicit splitter
+                                          tree (Section 2.2 multisplitter) instead of the
+                                          default cell table; same bucket ids */
 
 /* --------------------------------------------------------------- whole sorts */
 
@@ -167,7 +170,8 @@ typedef struct ams_stats {
 #define AMS_K_BINPACK 7
 #define AMS_K_SCATTER 8
 #define AMS_K_BASECASE 9
-#define AMS_K_COUNT 10
+#define AMS_K_TABLE 10        /* cell table of the splitters (classifier start) */
+#define AMS_K_COUNT 11
   float kernel_ms[AMS_K_COUNT];
   uint32_t kernel_calls[AMS_K_COUNT];
   uint64_t kernel_elems[AMS_K_COUNT];  /* elements read by that kind (for bandwidth) */

@@ -22,7 +22,7 @@ __all__ = [
     "stream_key", "sample_indices", "oversampling_factor", "sample",
     "rank_sort", "rank_sort_literal", "splitters", "classify", "classify_literal",
     "bucket_counts", "greedy_groups", "bin_pack", "eq_cut_threshold", "pieces",
-    "stable_partition", "Plan", "plan", "ams_sort", "default_basecase_cap",
+    "stable_partition", "piece_of_ids", "Plan", "plan", "ams_sort", "default_basecase_cap",
 ]
 
 KT_U32, KT_U64, KT_F32 = 0, 1, 2
@@ -362,6 +362,31 @@ def stable_partition(ids: np.ndarray) -> np.ndarray:
     return np.argsort(np.asarray(ids, dtype=np.int64), kind="stable")
 
 
+def piece_of_ids(counts, nbuckets: int, L: int, ends) -> np.ndarray:
+    """READING of the delivery of Section 6 ("the data splitting defined by the bucket
+    group is the input for data delivery"): elements are delivered to *pieces* -- a
+    group's buckets between heavy equality buckets form one piece, each heavy
+    equality bucket (see ``eq_cut_threshold``) is a piece of its own -- keeping input
+    order inside a piece.  Returns, for every bucket id, the first id of its piece
+    (a non-decreasing label, so a stable sort by it is the delivery order)."""
+    counts = [int(c) for c in counts]
+    nid = 2 * nbuckets - 1
+    tau = eq_cut_threshold(L)
+    label = np.zeros(nid, dtype=np.int64)
+    g0 = 0
+    for e in ends:
+        id_lo, id_hi = 2 * g0, min(2 * e, nid)
+        run = id_lo
+        for i in range(id_lo, id_hi):
+            if (i & 1) and counts[i] >= tau:
+                label[i] = i
+                run = i + 1
+            else:
+                label[i] = run
+        g0 = e
+    return label
+
+
 # --------------------------------------------------------------------------------------
 # Parameters of a run.  READINGS: `levels` is the largest number of distribution
 # levels the caller asks for; if n / prod(r) still exceeds the base-case capacity C,
@@ -452,7 +477,7 @@ def ams_sort(kt: int, keys: np.ndarray, pl: Plan, seed: int, vals=None, offsets=
             ids = classify(spl, B, seg)
             cnt = bucket_counts(ids, B)
             L, ends = bin_pack(cnt[0::2], pl.r[level - 1])
-            perm = stable_partition(ids)
+            perm = stable_partition(piece_of_ids(cnt, B, L, ends)[ids])
             t[lo:hi] = seg[perm]
             src_idx[lo:hi] = src_idx[lo:hi][perm]
             pcs = pieces(cnt, B, L, ends, lo)

@@ -23,8 +23,9 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "ams.h")
 U32, U64, F32 = 0, 1, 2
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_INTERNAL = range(7)
 FLAG_PHASE_TIMERS = 1
+FLAG_TREE_CLASSIFIER = 2
 KERNEL_KINDS = ("init", "setup", "sample_sort", "cross_rank", "splitters", "classify", "scan",
-                "binpack", "scatter", "basecase")
+                "binpack", "scatter", "basecase", "table")
 
 _lib = None
 
@@ -54,8 +55,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("levels_planned", ctypes.c_uint32), ("kernel_launches", ctypes.c_uint32),
                 ("segments", ctypes.c_uint32 * 8), ("basecase_items", ctypes.c_uint32 * 9),
                 ("device_status", ctypes.c_uint32), ("pad", ctypes.c_uint32),
-                ("kernel_ms", ctypes.c_float * 10), ("kernel_calls", ctypes.c_uint32 * 10),
-                ("kernel_elems", ctypes.c_uint64 * 10)]
+                ("kernel_ms", ctypes.c_float * 11), ("kernel_calls", ctypes.c_uint32 * 11),
+                ("kernel_elems", ctypes.c_uint64 * 11)]
 
     def as_dict(self):
         return {

@@ -117,6 +117,11 @@ struct LevelBufs {
   uint32_t* seg_L;
   uint32_t* seg_ng;
   BcItem* bc;
+  void* cls_head;
+  uint32_t* J2;
+  uint16_t* piece_of;
+  uint32_t* piece_start;
+  uint32_t* npieces;
 };
 
 struct Bufs {
@@ -150,6 +155,11 @@ size_t carve(const Plan& p, char* base, Bufs* b) {
     lb.seg_ng = c.take<uint32_t>(lp.nseg_cap);
     lb.bc = c.take<BcItem>(lp.bc_cap);
     lb.segs_next = c.take<Seg>(lp.next_cap + 1);
+    lb.cls_head = c.take<char>(lp.nseg_cap * 16);
+    lb.J2 = c.take<uint32_t>(lp.nseg_cap * kCellTable);
+    lb.piece_of = c.take<uint16_t>(lp.nseg_cap * lp.nid);
+    lb.piece_start = c.take<uint32_t>(lp.nseg_cap * lp.nid);
+    lb.npieces = c.take<uint32_t>(lp.nseg_cap);
   }
   return c.off + 256;
 }
@@ -306,6 +316,7 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
   cx->has_run = true;
 
   const bool f32 = rq->kt == AMS_F32;
+  const bool tree = (rq->opt.flags & AMS_FLAG_TREE_CLASSIFIER) != 0;
   const bool inplace = rq->keys_in == rq->keys_out;
   const int SM = cx->sm_count;
   Launcher ln{cx, s};
@@ -401,6 +412,12 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
     la.group_ends = nullptr;
     la.segs_next = lb.segs_next;
     la.bc = lb.bc;
+    la.cls_head = lb.cls_head;
+    la.J2 = lb.J2;
+    la.piece_of = lb.piece_of;
+    la.piece_start = lb.piece_start;
+    la.npieces = lb.npieces;
+    la.pieces_per_id = 0;
     la.nseg_cap = (uint32_t)lp.nseg_cap;
     la.samples_cap = (uint32_t)std::min<uint64_t>(lp.samples_cap, 0xFFFFFFFFull);
     la.items_cap = (uint32_t)std::min<uint64_t>(lp.items_cap, 0xFFFFFFFFull);
@@ -416,14 +433,16 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
     AMS_TRY(ln.end(launch_cross_rank(la, p.ksize, wide, s)));
     ln.begin(AMS_K_SPLITTERS);
     AMS_TRY(ln.end(launch_splitters(la, p.ksize, wide, s)));
+    ln.begin(AMS_K_TABLE);
+    AMS_TRY(ln.end(launch_table(la, p.ksize, seg_grid, s)));
     ln.begin(AMS_K_CLASSIFY);
-    AMS_TRY(ln.end(launch_classify(la, p.ksize, SM * 4, nullptr, s)));
+    AMS_TRY(ln.end(launch_classify(la, p.ksize, tree, SM * 4, nullptr, s)));
     ln.begin(AMS_K_SCAN);
     AMS_TRY(ln.end(launch_scan(la, SM * 8, s)));
     ln.begin(AMS_K_BINPACK);
     AMS_TRY(ln.end(launch_binpack(la, seg_grid, s)));
     ln.begin(AMS_K_SCATTER);
-    AMS_TRY(ln.end(launch_scatter(la, p.ksize, p.pairs, SM * 2, s)));
+    AMS_TRY(ln.end(launch_scatter(la, p.ksize, p.pairs, tree, SM * 2, s)));
     if ((st = run_basecase(la.dst, la.vdst, lb.bc, &b.ctr[l], 0, lp.bc_cap)) != AMS_OK) return st;
   }
   return AMS_OK;
@@ -453,6 +472,11 @@ struct StepWs {
   uint32_t* seg_ng;
   BcItem* bc;
   Seg* segs_next;
+  void* cls_head;
+  uint32_t* J2;
+  uint16_t* piece_of;
+  uint32_t* piece_start;
+  uint32_t* npieces;
 };
 
 __global__ void k_step_prepare(Seg* segs, LevelCounters* ctr, uint32_t begin, uint32_t end,
@@ -502,6 +526,11 @@ static ams_status step_ws(Context* cx, uint64_t samples, uint32_t B, uint64_t it
     w->seg_ng = c.take<uint32_t>(1);
     w->bc = c.take<BcItem>(2 * (uint64_t)nid + 16);
     w->segs_next = c.take<Seg>(2 * (uint64_t)nid + 16);
+    w->cls_head = c.take<char>(16);
+    w->J2 = c.take<uint32_t>(kCellTable);
+    w->piece_of = c.take<uint16_t>(nid + 1);
+    w->piece_start = c.take<uint32_t>(nid + 1);
+    w->npieces = c.take<uint32_t>(1);
     return c.off + 256;
   };
   const size_t need = lay(nullptr);
@@ -541,6 +570,12 @@ static LevelArgs step_level(Context* cx, const StepWs& w, uint32_t B, uint32_t a
   la.seg_ng = w.seg_ng;
   la.segs_next = w.segs_next;
   la.bc = w.bc;
+  la.cls_head = w.cls_head;
+  la.J2 = w.J2;
+  la.piece_of = w.piece_of;
+  la.piece_start = w.piece_start;
+  la.npieces = w.npieces;
+  la.pieces_per_id = 0;
   la.status = cx->d_status;
   la.nseg_cap = 1;
   la.samples_cap = 0xFFFFFFFFu;
@@ -842,7 +877,8 @@ ams_status ams_step_classify(const void* d_keys, uint64_t n, ams_key_type kt, co
   k_step_prepare<<<1, 32, 0, s>>>(w.segs, w.ctr, 0, (uint32_t)n, w.srank, 0);
   AMS_TRY(cudaGetLastError());
   AMS_TRY(launch_setup(la, s));
-  AMS_TRY(launch_classify(la, ks, cx->sm_count * 4, d_ids, s));
+  AMS_TRY(launch_table(la, ks, 1, s));
+  AMS_TRY(launch_classify(la, ks, false, cx->sm_count * 4, d_ids, s));
   AMS_TRY(launch_scan(la, cx->sm_count * 8, s));
   AMS_TRY(cudaMemcpyAsync(d_counts, w.totals, (size_t)la.nid * 4, cudaMemcpyDeviceToDevice, s));
   return AMS_OK;
@@ -898,10 +934,12 @@ ams_status ams_step_partition(const void* d_in, void* d_out, const uint64_t* d_v
   k_step_prepare<<<1, 32, 0, s>>>(w.segs, w.ctr, 0, (uint32_t)n, w.srank, 0);
   AMS_TRY(cudaGetLastError());
   AMS_TRY(launch_setup(la, s));
-  AMS_TRY(launch_classify(la, ks, cx->sm_count * 4, nullptr, s));
+  la.pieces_per_id = 1;  // deliver bucket by bucket
+  AMS_TRY(launch_table(la, ks, 1, s));
+  AMS_TRY(launch_classify(la, ks, false, cx->sm_count * 4, nullptr, s));
   AMS_TRY(launch_scan(la, cx->sm_count * 8, s));
   AMS_TRY(launch_binpack(la, 1, s));
-  AMS_TRY(launch_scatter(la, ks, d_vals_in != nullptr, cx->sm_count * 2, s));
+  AMS_TRY(launch_scatter(la, ks, d_vals_in != nullptr, false, cx->sm_count * 2, s));
   return AMS_OK;
 }
 

@@ -26,6 +26,7 @@ constexpr int kMaxLevels = 8;
 constexpr int kSampleTile = 2048;       // keys per locally sorted sample tile
 constexpr uint32_t kCopyChunk = 65536;  // elements per copy work item
 constexpr int kMaxBuckets = 2048;       // largest b*r per level
+constexpr uint32_t kCellTable = 4096;   // cells of the table classifier
 constexpr int kThrCount = 48;           // oversampling thresholds 10^(a/1.6)
 
 // base-case work item kinds
@@ -93,6 +94,12 @@ struct LevelArgs {
   uint32_t* seg_L;    // per segment: optimal group bound L*
   uint32_t* seg_ng;   // per segment: number of groups
   uint32_t* group_ends;  // optional, r per segment
+  void* cls_head;        // per segment: table-classifier parameters (ClsHead<K>)
+  uint32_t* J2;          // per segment: kCells cell-table words
+  uint16_t* piece_of;    // per segment x id: piece index of the bucket
+  uint32_t* piece_start; // per segment x piece: first position (relative)
+  uint32_t* npieces;     // per segment: number of pieces
+  uint32_t pieces_per_id;  // 1: every bucket is its own piece (step calls)
   Seg* segs_next;
   BcItem* bc;
   LevelCounters* ctr;
@@ -198,15 +205,17 @@ cudaError_t launch_setup(const LevelArgs& a, cudaStream_t s);
 cudaError_t launch_sample_sort(const LevelArgs& a, int ksize, int grid, cudaStream_t s);
 cudaError_t launch_cross_rank(const LevelArgs& a, int ksize, int grid, cudaStream_t s);
 cudaError_t launch_splitters(const LevelArgs& a, int ksize, int grid, cudaStream_t s);
-cudaError_t launch_classify(const LevelArgs& a, int ksize, int grid, uint16_t* ids_out,
+cudaError_t launch_table(const LevelArgs& a, int ksize, int grid, cudaStream_t s);
+cudaError_t launch_classify(const LevelArgs& a, int ksize, bool tree, int grid, uint16_t* ids_out,
                             cudaStream_t s);
 cudaError_t launch_scan(const LevelArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_binpack(const LevelArgs& a, int grid, cudaStream_t s);
-cudaError_t launch_scatter(const LevelArgs& a, int ksize, bool pairs, int grid, cudaStream_t s);
+cudaError_t launch_scatter(const LevelArgs& a, int ksize, bool pairs, bool tree, int grid, cudaStream_t s);
 cudaError_t launch_basecase(const BaseArgs& a, int ksize, bool pairs, int grid, cudaStream_t s);
 
 // shared-memory bytes each kernel needs (for occupancy and opt-in)
-size_t scatter_smem_bytes(int ksize, bool pairs, uint32_t B);
+size_t scatter_smem_bytes(int ksize, bool pairs, uint32_t B, bool tree);
+size_t classify_smem_bytes(int ksize, uint32_t B, bool tree);
 size_t basecase_smem_bytes(int ksize, bool pairs);
 uint32_t basecase_max_cap(int ksize, bool pairs);
 

@@ -1,0 +1,130 @@
+// Bucket classification of Section 6 (partition into b*r buckets, Section 2.2
+// branch-free multisplitter) with the equality buckets of Appendix D.  For a key x
+// and sorted splitters s_0..s_{B-2}: j = #{i : s_i < x}; id = 2j + [j < B-1 and
+// x == s_j].  Two implementations give the same ids:
+//
+//  * tree:  the implicit search tree of the paper's multisplitter, i <- 2i + [t_i < x]
+//           for log2(B') levels (B' = B rounded up to a power of two);
+//  * table: a radix-assisted start.  The splitter range [s_0, s_{B-2}] is cut into
+//           4096 equal-width cells; J[c] = #{splitters below cell c}.  A key's cell
+//           bounds j to [J[c], J[c+1]], and a branch-free binary search over that
+//           short span (a fixed number of steps per segment: the widest span of the
+//           segment) finishes it.  Cost: one table load plus a few compares instead of
+//           log2(B') dependent loads.
+#pragma once
+
+#include "ams_internal.cuh"
+
+namespace ams {
+
+constexpr int kCellBits = 12;
+constexpr uint32_t kCells = 1u << kCellBits;
+static_assert(kCells == kCellTable, "cell table size");
+
+// Per-segment parameters of the table classifier (written by k_table).
+template <typename K>
+struct ClsHead {
+  K lo;            // smallest splitter
+  uint32_t sh;     // cell = (x - lo) >> sh
+  uint32_t steps;  // binary-search steps that resolve the widest span
+};
+
+// J2[c] = J[c] | J[c+1] << 16, c < kCells.
+template <typename K>
+__device__ __forceinline__ uint32_t table_classify(const uint32_t* J2, const K* spl, K lo, uint32_t sh,
+                                                   uint32_t steps, uint32_t B, K x) {
+  constexpr int kBits = 8 * sizeof(K);
+  const K d = x - lo;
+  uint32_t c;
+  if (x < lo) {
+    c = 0;
+  } else {
+    const K q = sh >= (uint32_t)kBits ? K(0) : (d >> sh);
+    c = q >= (K)kCells ? kCells - 1 : (uint32_t)q;
+  }
+  const uint32_t jj = J2[c];
+  uint32_t base = jj & 0xFFFFu;
+  uint32_t len = (jj >> 16) - base;
+  for (uint32_t s = 0; s < steps; ++s) {
+    const uint32_t half = len >> 1;
+    const bool lt = len > 0 && spl[base + half] < x;
+    base = lt ? base + half + 1 : base;
+    len = lt ? len - half - 1 : half;
+  }
+  const uint32_t eq = (base < B - 1) && (spl[base] == x);
+  return 2 * base + eq;
+}
+
+template <typename K>
+__device__ __forceinline__ uint32_t tree_classify(const K* tree, const K* spl, uint32_t logBp, uint32_t B,
+                                                  K x) {
+  uint32_t i = 1;
+#pragma unroll 4
+  for (uint32_t d = 0; d < logBp; ++d) i = 2 * i + (tree[i] < x ? 1u : 0u);
+  const uint32_t j = i - (1u << logBp);
+  const uint32_t eq = (j < B - 1) && (spl[j] == x);
+  return 2 * j + eq;
+}
+
+// Shared-memory image of one segment's classifier.  Layout from a 16-byte aligned
+// base (the table comes first because it is copied with 16-byte stores):
+//   J2    : kCells words (table mode only)
+//   spl   : Bp keys (B-1 splitters, then the largest key as padding)
+//   tree  : Bp keys (tree mode only; node 0 unused)
+template <typename K>
+struct ClsSmem {
+  K* spl;
+  K* tree;
+  uint32_t* J2;
+  K lo;
+  uint32_t sh, steps;
+};
+
+template <typename K>
+__host__ __device__ constexpr size_t cls_smem_bytes(uint32_t Bp, bool tree) {
+  return (size_t)Bp * sizeof(K) * (tree ? 2 : 1) + (tree ? 0 : (size_t)kCells * 4);
+}
+
+// Points cs into the classifier block at `base` (16-byte aligned).
+template <typename K>
+__device__ __forceinline__ void cls_bind(ClsSmem<K>& cs, unsigned char* base, uint32_t Bp, bool tree) {
+  cs.J2 = tree ? nullptr : (uint32_t*)base;
+  cs.spl = (K*)(base + (tree ? 0 : (size_t)kCells * 4));
+  cs.tree = tree ? cs.spl + Bp : nullptr;
+}
+
+// Loads segment g's classifier into shared memory (block-wide; ends with a barrier).
+template <typename K>
+__device__ __forceinline__ void load_classifier(ClsSmem<K>& cs, const K* spl_g, const ClsHead<K>* head,
+                                                const uint32_t* J2_g, uint32_t B, uint32_t logBp,
+                                                bool tree, int NT) {
+  const uint32_t Bp = 1u << logBp;
+  for (uint32_t i = threadIdx.x; i < Bp; i += NT) cs.spl[i] = i < B - 1 ? spl_g[i] : key_max<K>();
+  if (!tree) {
+    const uint4* s4 = (const uint4*)J2_g;
+    uint4* d4 = (uint4*)cs.J2;
+    for (uint32_t i = threadIdx.x; i < kCells / 4; i += NT) d4[i] = s4[i];
+    const ClsHead<K> h = *head;
+    cs.lo = h.lo;
+    cs.sh = h.sh;
+    cs.steps = h.steps;
+  }
+  __syncthreads();
+  if (tree) {
+    for (uint32_t k = 1 + threadIdx.x; k < Bp; k += NT) {
+      const uint32_t d = 31 - __clz((int)k);
+      const uint32_t idx = ((2 * (k - (1u << d)) + 1) << (logBp - d - 1)) - 1;
+      cs.tree[k] = cs.spl[idx];  // padding entries hold the largest key
+    }
+    __syncthreads();
+  }
+}
+
+template <typename K>
+__device__ __forceinline__ uint32_t classify(const ClsSmem<K>& cs, bool tree, uint32_t logBp, uint32_t B,
+                                             K x) {
+  return tree ? tree_classify<K>(cs.tree, cs.spl, logBp, B, x)
+              : table_classify<K>(cs.J2, cs.spl, cs.lo, cs.sh, cs.steps, B, x);
+}
+
+}  // namespace ams

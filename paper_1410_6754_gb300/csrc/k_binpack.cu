@@ -192,8 +192,48 @@ __global__ void __launch_bounds__(1024) k_binpack(LevelArgs a) {
     }
     if (a.group_ends)
       for (uint32_t i = tid; i < a.r; i += NT) a.group_ends[(size_t)g * a.r + i] = i < ng ? ends[i] : B;
-    // pieces of every group
+    // pieces of every group (one thread per group): a heavy equality bucket cuts its
+    // group into [run before] [the bucket, final] [run after]; runs that cover no
+    // bucket id (a group ending in a heavy equality bucket) are not made
     const uint32_t tau = max(2u, (uint32_t)(Lstar >> 4));
+    uint16_t* pof = a.piece_of + (size_t)g * nid;
+    uint32_t* pst = a.piece_start + (size_t)g * nid;
+    if (a.pieces_per_id) {
+      for (uint32_t i = tid; i < nid; i += NT) {
+        pof[i] = (uint16_t)i;
+        pst[i] = bst_s[i];
+      }
+      if (tid == 0) a.npieces[g] = nid;
+    } else {
+      uint32_t* pc_s = ends + a.r;  // r counters after the group ends
+      for (uint32_t k = tid; k < ng; k += NT) {
+        const uint32_t gs = k ? ends[k - 1] : 0, ge = ends[k];
+        const uint32_t id_lo = 2 * gs, id_hi = min(2 * ge, nid);
+        uint32_t c = 1;
+        for (uint32_t i = id_lo | 1; i < id_hi; i += 2)
+          if (cnt_s[i] >= tau) c += (i + 1 < id_hi) ? 2 : 1;
+        pc_s[k] = c;
+      }
+      __syncthreads();
+      const uint32_t P = block_scan_array<NT, uint32_t>(pc_s, ng, ws);
+      if (tid == 0) a.npieces[g] = P;
+      for (uint32_t k = tid; k < ng; k += NT) {
+        const uint32_t gs = k ? ends[k - 1] : 0, ge = ends[k];
+        const uint32_t id_lo = 2 * gs, id_hi = min(2 * ge, nid);
+        uint32_t cur = pc_s[k];
+        pst[cur] = bst_s[id_lo];
+        for (uint32_t i = id_lo; i < id_hi; ++i) {
+          if ((i & 1) && cnt_s[i] >= tau) {
+            pof[i] = (uint16_t)(cur + 1);
+            pst[cur + 1] = bst_s[i];
+            if (i + 1 < id_hi) pst[cur + 2] = bst_s[i + 1];
+            cur += 2;
+          } else {
+            pof[i] = (uint16_t)cur;
+          }
+        }
+      }
+    }
     for (uint32_t k = tid; k < ng; k += NT) {
       Emitter em{&a, sg.begin, 0, 0};
       const uint32_t gs = k ? ends[k - 1] : 0, ge = ends[k];
@@ -244,7 +284,7 @@ cudaError_t launch_init(const InitArgs& a, int grid, cudaStream_t s) {
 cudaError_t launch_binpack(const LevelArgs& a, int grid, cudaStream_t s) {
   // dynamic + static shared memory may pass 48 KB even when the dynamic part alone
   // does not, so the limit is always raised to what the launch asks for
-  const size_t sm = (size_t)(a.nid + a.nid + 1 + a.B + 1 + a.r) * 4;
+  const size_t sm = (size_t)(a.nid + a.nid + 1 + a.B + 1 + 2 * a.r) * 4;
   cudaError_t e = cudaFuncSetAttribute(k_binpack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k_binpack<<<grid, 1024, sm, s>>>(a);

@@ -1,54 +1,82 @@
 // Partitioning and delivery of one distribution level (Section 6; equality buckets of
 // Appendix D; prefix-sum delivery of Section 4.3):
-//   classify  every key of a chunk gets its bucket id by descending an implicit
-//             search tree over the splitters (i <- 2i + [t_i < x]); an extra compare
-//             against splitter j sends keys equal to it to equality bucket 2j+1.
-//             Per-chunk bucket counts go to the count table.
+//   table     per segment: the cell table of the table classifier (classifier.cuh)
+//   classify  every key of a chunk gets its bucket id; per-chunk bucket counts
 //   scan      per (segment, id): exclusive prefix of the counts over the segment's
-//             chunks (where each chunk's run of a bucket starts) and bucket totals.
-//   scatter   stable delivery: each key goes to bucket start + chunk offset + its
-//             rank among the chunk's keys of the same id (input order), staged per
-//             tile in shared memory so that every bucket receives one contiguous run.
+//             chunks, and the bucket totals
+//   scatter   group-wise delivery: every key goes to its *piece* (a run of buckets of
+//             one group, or a final equality bucket; the pieces are made by the
+//             bin-packing kernel), at piece start + chunk offset + its rank among the
+//             chunk's keys of that piece in input order.  Per tile of keys the ranks
+//             come from warp-level match ranking and a scan over (piece, warp)
+//             counters; keys are staged piece-major in shared memory so that every
+//             piece receives one contiguous run per tile.
+#include "classifier.cuh"
 #include "cta_utils.cuh"
 
 namespace ams {
 
-// Implicit tree over the padded splitters (index 0 unused): node k at depth d holds
-// splitter (2 (k - 2^d) + 1) 2^(L-d-1) - 1; entries past B-1 hold the largest key.
+// ---------------------------------------------------------------------------- table
 template <typename K>
-__device__ __forceinline__ void build_tree(const K* spl_g, uint32_t B, uint32_t logBp, K* tree,
-                                           K* spl_s, int NT) {
-  for (uint32_t i = threadIdx.x; i < B - 1; i += NT) spl_s[i] = spl_g[i];
-  __syncthreads();
-  const uint32_t Bp = 1u << logBp;
-  for (uint32_t k = 1 + threadIdx.x; k < Bp; k += NT) {
-    const uint32_t d = 31 - __clz((int)k);
-    const uint32_t idx = ((2 * (k - (1u << d)) + 1) << (logBp - d - 1)) - 1;
-    tree[k] = idx < B - 1 ? spl_s[idx] : key_max<K>();
+__global__ void __launch_bounds__(512) k_table(LevelArgs a) {
+  constexpr int NT = 512;
+  __shared__ K spl_s[kMaxBuckets];
+  __shared__ uint16_t J_s[kCells + 1];
+  __shared__ uint32_t ws[NT / 32 + 1];
+  const uint32_t nseg = a.ctr->nseg;
+  const uint32_t B = a.B;
+  for (uint32_t g = blockIdx.x; g < nseg; g += gridDim.x) {
+    const K* spl_g = (const K*)a.spl + (size_t)g * (B - 1);
+    for (uint32_t i = threadIdx.x; i < B - 1; i += NT) spl_s[i] = spl_g[i];
+    __syncthreads();
+    const K lo = spl_s[0], hi = spl_s[B - 2];
+    const int nb = bitlen<K>((K)(hi - lo));
+    const uint32_t sh = nb > kCellBits ? (uint32_t)(nb - kCellBits) : 0u;
+    for (uint32_t c = threadIdx.x; c <= kCells; c += NT) {
+      uint32_t j;
+      if (c == 0) {
+        j = 0;
+      } else if (c == kCells || ((K)c << sh) > (K)(key_max<K>() - lo)) {
+        j = B - 1;
+      } else {
+        const K edge = lo + ((K)c << sh);  // first key of cell c
+        uint32_t l = 0, h = B - 1;           // #{splitters < edge}
+        while (l < h) {
+          const uint32_t m = (l + h) >> 1;
+          if (spl_s[m] < edge) l = m + 1; else h = m;
+        }
+        j = l;
+      }
+      J_s[c] = (uint16_t)j;
+    }
+    __syncthreads();
+    uint32_t* J2 = a.J2 + (size_t)g * kCells;
+    uint32_t span = 0;
+    for (uint32_t c = threadIdx.x; c < kCells; c += NT) {
+      J2[c] = (uint32_t)J_s[c] | ((uint32_t)J_s[c + 1] << 16);
+      span = max(span, (uint32_t)J_s[c + 1] - J_s[c]);
+    }
+    const uint32_t mspan = block_reduce_max<NT, uint32_t>(span, ws);
+    if (threadIdx.x == 0) {
+      ClsHead<K> h;
+      h.lo = lo;
+      h.sh = sh;
+      h.steps = mspan ? 32 - __clz((int)mspan) : 0;
+      ((ClsHead<K>*)a.cls_head)[g] = h;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-}
-
-template <typename K>
-__device__ __forceinline__ uint32_t classify_key(const K* tree, const K* spl, uint32_t logBp,
-                                                 uint32_t B, K x) {
-  uint32_t i = 1;
-#pragma unroll 4
-  for (uint32_t d = 0; d < logBp; ++d) i = 2 * i + (tree[i] < x ? 1u : 0u);
-  const uint32_t j = i - (1u << logBp);
-  const uint32_t eq = (j < B - 1) && (spl[j] == x);
-  return 2 * j + eq;
 }
 
 // ------------------------------------------------------------------------- classify
-template <typename K>
+template <typename K, bool TREE>
 __global__ void __launch_bounds__(512) k_classify(LevelArgs a, uint16_t* ids_out) {
   constexpr int NT = 512;
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t Bp = 1u << a.logBp;
-  K* tree = (K*)smem;
-  K* spl_s = tree + Bp;
-  uint32_t* hist = (uint32_t*)(spl_s + Bp);
+  ClsSmem<K> cs;
+  cls_bind<K>(cs, smem, Bp, TREE);
+  uint32_t* hist = (uint32_t*)(smem + cls_smem_bytes<K>(Bp, TREE));
   const uint32_t nseg = a.ctr->nseg;
   const uint32_t items = a.ctr->items;
   const K* src = (const K*)a.src;
@@ -61,7 +89,8 @@ __global__ void __launch_bounds__(512) k_classify(LevelArgs a, uint16_t* ids_out
     const Seg sg = a.segs[g];
     if (g != cur_g) {
       __syncthreads();
-      build_tree<K>((const K*)a.spl + (size_t)g * (a.B - 1), a.B, a.logBp, tree, spl_s, NT);
+      load_classifier<K>(cs, (const K*)a.spl + (size_t)g * (a.B - 1), (const ClsHead<K>*)a.cls_head + g,
+                         a.J2 + (size_t)g * kCells, a.B, a.logBp, TREE, NT);
       cur_g = g;
     }
     for (uint32_t i = threadIdx.x; i < a.nid; i += NT) hist[i] = 0;
@@ -76,18 +105,21 @@ __global__ void __launch_bounds__(512) k_classify(LevelArgs a, uint16_t* ids_out
     const uint32_t nv = (hi - b0) / V;
     const uint32_t b1 = b0 + nv * V;
     auto put = [&](uint32_t pos, K x, bool valid) {
-      const uint32_t id = valid ? classify_key<K>(tree, spl_s, a.logBp, a.B, order_in<K>(x, a.tf_src))
-                                : 0xFFFFFFFFu;
-      const uint32_t peers = __match_any_sync(0xFFFFFFFFu, id);
-      if (valid) {
-        if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&hist[id], (uint32_t)__popc(peers));
-        if (ids_out) ids_out[pos - a.segs[0].begin] = (uint16_t)id;
+      const uint32_t id = valid ? classify<K>(cs, TREE, a.logBp, a.B, order_in<K>(x, a.tf_src)) : 0xFFFFFFFFu;
+      // a warp whose keys all share one bucket adds them with one atomic
+      const uint32_t id0 = __shfl_sync(0xFFFFFFFFu, id, 0);
+      const uint32_t vm = __ballot_sync(0xFFFFFFFFu, valid);
+      if (__all_sync(0xFFFFFFFFu, !valid || id == id0)) {
+        if (lane == 0 && vm) atomicAdd(&hist[id0], (uint32_t)__popc(vm));
+      } else if (valid) {
+        atomicAdd(&hist[id], 1u);
       }
+      if (ids_out && valid) ids_out[pos - a.segs[0].begin] = (uint16_t)id;
     };
-    // scalar head and tail (at most 2*(V-1) keys)
-    for (uint32_t wb = wbase; wb < (b0 - lo) + (hi - b1); wb += NT) {
+    const uint32_t nscalar = (b0 - lo) + (hi - b1);
+    for (uint32_t wb = wbase; wb < nscalar; wb += NT) {
       const uint32_t e = wb + lane;
-      const bool valid = e < (b0 - lo) + (hi - b1);
+      const bool valid = e < nscalar;
       const uint32_t pos = e < (b0 - lo) ? lo + e : b1 + (e - (b0 - lo));
       put(pos, valid ? src[pos] : K(0), valid);
     }
@@ -142,31 +174,28 @@ __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
 
 // -------------------------------------------------------------------------- scatter
 // Block of 256 threads = 8 warps; warp w owns keys [w*32R, (w+1)*32R) of a tile of
-// 256R keys, lane l of round q holds key w*32R + 32q + l.  Per tile:
-//  1. classify; rank each key among the keys of its warp with the same id that come
-//     earlier (match_any + popc, per-warp counters cnt[id][w]),
-//  2. scan the counters over (id, warp) -> tile position of every key,
-//  3. stage keys by tile position (bucket-major, input order inside a bucket),
-//  4. write each bucket's run to run_off[id] onward, then advance run_off.
+// 256R keys; lane l of round q holds key w*32R + 32q + l.
 template <typename K, bool PAIRS>
 struct ScatterCfg {
   static constexpr int NT = 256;
-  static constexpr int R = PAIRS ? 8 : (sizeof(K) == 4 ? 32 : 16);
+  static constexpr int W = NT / 32;
+  static constexpr int R = PAIRS ? 8 : 16;
   static constexpr int TILE = NT * R;
 };
 
-template <typename K, bool PAIRS>
+template <typename K, bool PAIRS, bool TREE>
 __host__ __device__ constexpr size_t scatter_smem_layout(uint32_t B, size_t* off) {
-  // offsets: tree, spl, cnt, tstart, run_off, stage_key, stage_id, stage_val, ws
+  // offsets: classifier, piece_of, cnt, tstart, run_off, stage_key, stage_id, stage_val, ws
   using C = ScatterCfg<K, PAIRS>;
   uint32_t Bp = 1;
   while (Bp < B) Bp <<= 1;
   const uint32_t nid = 2 * B - 1;
+  const uint32_t S = (nid + 2) & ~1u;  // counter row stride (entries)
   size_t o = 0;
-  off[0] = o; o += (size_t)Bp * sizeof(K);
-  off[1] = o; o += (size_t)Bp * sizeof(K);
+  off[0] = o; o += cls_smem_bytes<K>(Bp, TREE);
+  off[1] = o; o += (size_t)nid * 2;
   o = (o + 15) & ~(size_t)15;
-  off[2] = o; o += (size_t)(nid + 1) * 16;
+  off[2] = o; o += (size_t)C::W * S * 2;
   off[3] = o; o += (size_t)(nid + 2) * 2;
   o = (o + 15) & ~(size_t)15;
   off[4] = o; o += (size_t)nid * 4;
@@ -179,17 +208,20 @@ __host__ __device__ constexpr size_t scatter_smem_layout(uint32_t B, size_t* off
   return o;
 }
 
-template <typename K, bool PAIRS>
+template <typename K, bool PAIRS, bool TREE>
 __global__ void __launch_bounds__(256) k_scatter(LevelArgs a) {
   using Cfg = ScatterCfg<K, PAIRS>;
   constexpr int NT = Cfg::NT, R = Cfg::R, TILE = Cfg::TILE;
   extern __shared__ __align__(16) unsigned char smem[];
   size_t off[9];
-  scatter_smem_layout<K, PAIRS>(a.B, off);
-  K* tree = (K*)(smem + off[0]);
-  K* spl_s = (K*)(smem + off[1]);
+  scatter_smem_layout<K, PAIRS, TREE>(a.B, off);
+  const uint32_t Bp = 1u << a.logBp;
+  const uint32_t nid = a.nid;
+  const uint32_t S = (nid + 2) & ~1u;
+  ClsSmem<K> cs;
+  cls_bind<K>(cs, smem + off[0], Bp, TREE);
+  uint16_t* piece_of = (uint16_t*)(smem + off[1]);
   uint16_t* cnt = (uint16_t*)(smem + off[2]);
-  uint4* cnt4 = (uint4*)(smem + off[2]);
   uint16_t* tstart = (uint16_t*)(smem + off[3]);
   uint32_t* run_off = (uint32_t*)(smem + off[4]);
   K* stage_key = (K*)(smem + off[5]);
@@ -199,12 +231,12 @@ __global__ void __launch_bounds__(256) k_scatter(LevelArgs a) {
 
   const uint32_t nseg = a.ctr->nseg;
   const uint32_t items = a.ctr->items;
-  const uint32_t nid = a.nid;
   const K* src = (const K*)a.src;
   K* dst = (K*)a.dst;
   const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const uint32_t ltm = lanemask_lt();
   uint32_t cur_g = 0xFFFFFFFFu;
+  uint32_t P = 0;
 
   for (uint32_t k = blockIdx.x; k < items; k += gridDim.x) {
     const uint32_t g = find_seg<&SegInfo::item_off>(a.sinfo, nseg, k);
@@ -212,20 +244,31 @@ __global__ void __launch_bounds__(256) k_scatter(LevelArgs a) {
     const Seg sg = a.segs[g];
     if (g != cur_g) {
       __syncthreads();
-      build_tree<K>((const K*)a.spl + (size_t)g * (a.B - 1), a.B, a.logBp, tree, spl_s, NT);
+      const uint16_t* pof = a.piece_of + (size_t)g * nid;
+      for (uint32_t i = tid; i < nid; i += NT) piece_of[i] = pof[i];
+      load_classifier<K>(cs, (const K*)a.spl + (size_t)g * (a.B - 1), (const ClsHead<K>*)a.cls_head + g,
+                         a.J2 + (size_t)g * kCells, a.B, a.logBp, TREE, NT);
+      P = a.npieces[g];
       cur_g = g;
     }
-    const uint32_t* bst = a.totals + (size_t)g * nid;
+    // run offset of every piece for this chunk: piece start + earlier chunks' keys of
+    // all the piece's buckets
+    const uint32_t* pst = a.piece_start + (size_t)g * nid;
+    for (uint32_t p = tid; p < P; p += NT) run_off[p] = sg.begin + pst[p];
+    __syncthreads();
     const uint32_t* coff = a.counts + (size_t)k * nid;
-    for (uint32_t i = tid; i < nid; i += NT) run_off[i] = sg.begin + bst[i] + coff[i];
+    for (uint32_t i = tid; i < nid; i += NT) {
+      const uint32_t c = coff[i];
+      if (c) atomicAdd(&run_off[piece_of[i]], c);
+    }
     const uint32_t lo = sg.begin + (k - si.item_off) * a.CH;
     const uint32_t hi = (uint32_t)min((uint64_t)lo + a.CH, (uint64_t)sg.end);
     __syncthreads();
 
     for (uint32_t t0 = lo; t0 < hi; t0 += TILE) {
       const uint32_t tn = min((uint32_t)TILE, hi - t0);
-      for (uint32_t i = tid; i < nid + 1; i += NT) cnt4[i] = make_uint4(0, 0, 0, 0);
-      // 1. load, classify, rank inside the warp
+      for (uint32_t i = tid; i < (uint32_t)Cfg::W * S / 2; i += NT) ((uint32_t*)cnt)[i] = 0;
+      // 1. load, classify, rank among the warp's keys of the same piece
       K x[R];
       uint64_t v[PAIRS ? R : 1];
 #pragma unroll
@@ -236,30 +279,30 @@ __global__ void __launch_bounds__(256) k_scatter(LevelArgs a) {
       }
       __syncthreads();
       uint32_t pk[R];
+      uint16_t* crow = cnt + w * S;
 #pragma unroll
       for (int q = 0; q < R; ++q) {
         const uint32_t p = w * 32 * R + q * 32 + lane;
-        const uint32_t id = p < tn ? classify_key<K>(tree, spl_s, a.logBp, a.B, x[q]) : nid;
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, id);
+        const uint32_t pc = p < tn ? piece_of[classify<K>(cs, TREE, a.logBp, a.B, x[q])] : P;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, pc);
         const uint32_t rk = __popc(peers & ltm);
-        uint16_t* c = &cnt[id * 8 + w];
-        const uint32_t base = *c;
+        const uint32_t base = crow[pc];
         __syncwarp();
-        if (rk == 0) *c = (uint16_t)(base + __popc(peers));
+        if (rk == 0) crow[pc] = (uint16_t)(base + __popc(peers));
         __syncwarp();
-        pk[q] = (id << 16) | (base + rk);
+        pk[q] = (pc << 16) | (base + rk);
       }
       __syncthreads();
-      // 2. per-id totals, scan over ids, per-warp starts
-      for (uint32_t i = tid; i < nid + 1; i += NT) {
-        const uint4 c4 = cnt4[i];
-        const uint32_t s = (c4.x & 0xFFFF) + (c4.x >> 16) + (c4.y & 0xFFFF) + (c4.y >> 16) +
-                           (c4.z & 0xFFFF) + (c4.z >> 16) + (c4.w & 0xFFFF) + (c4.w >> 16);
-        tstart[i] = (uint16_t)s;
+      // 2. piece totals, scan over pieces, per-warp starts
+      for (uint32_t p = tid; p <= P; p += NT) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int j = 0; j < Cfg::W; ++j) s += cnt[j * S + p];
+        tstart[p] = (uint16_t)s;
       }
       __syncthreads();
       {
-        const uint32_t m = nid + 1;
+        const uint32_t m = P + 1;
         const uint32_t chunk = (m + NT - 1) / NT;
         const uint32_t b = tid * chunk, e = min(b + chunk, m);
         uint32_t s = 0;
@@ -274,60 +317,59 @@ __global__ void __launch_bounds__(256) k_scatter(LevelArgs a) {
         if (tid == 0) tstart[m] = (uint16_t)total;
       }
       __syncthreads();
-      for (uint32_t i = tid; i < nid + 1; i += NT) {
-        uint4 c4 = cnt4[i];
-        uint32_t base = tstart[i];
-        uint32_t h[8] = {c4.x & 0xFFFF, c4.x >> 16, c4.y & 0xFFFF, c4.y >> 16,
-                         c4.z & 0xFFFF, c4.z >> 16, c4.w & 0xFFFF, c4.w >> 16};
+      for (uint32_t p = tid; p <= P; p += NT) {
+        uint32_t base = tstart[p];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const uint32_t t = h[j];
-          h[j] = base;
+        for (int j = 0; j < Cfg::W; ++j) {
+          const uint32_t t = cnt[j * S + p];
+          cnt[j * S + p] = (uint16_t)base;
           base += t;
         }
-        c4.x = h[0] | (h[1] << 16);
-        c4.y = h[2] | (h[3] << 16);
-        c4.z = h[4] | (h[5] << 16);
-        c4.w = h[6] | (h[7] << 16);
-        cnt4[i] = c4;
       }
       __syncthreads();
-      // 3. stage by tile position
+      // 3. stage by tile position (piece-major, input order inside a piece)
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        const uint32_t id = pk[q] >> 16;
-        const uint32_t pos = cnt[id * 8 + w] + (pk[q] & 0xFFFF);
+        const uint32_t pc = pk[q] >> 16;
+        const uint32_t pos = crow[pc] + (pk[q] & 0xFFFF);
         stage_key[pos] = x[q];
-        stage_id[pos] = (uint16_t)id;
+        stage_id[pos] = (uint16_t)pc;
         if constexpr (PAIRS) stage_val[pos] = v[q];
       }
       __syncthreads();
-      // 4. one contiguous run per bucket
+      // 4. one contiguous run per piece
       for (uint32_t p = tid; p < tn; p += NT) {
-        const uint32_t id = stage_id[p];
-        const uint32_t d = run_off[id] + (p - tstart[id]);
+        const uint32_t pc = stage_id[p];
+        const uint32_t d = run_off[pc] + (p - tstart[pc]);
         dst[d] = stage_key[p];
         if constexpr (PAIRS) a.vdst[d] = stage_val[p];
       }
       __syncthreads();
-      for (uint32_t i = tid; i < nid; i += NT) run_off[i] += (uint32_t)tstart[i + 1] - tstart[i];
+      for (uint32_t p = tid; p < P; p += NT) run_off[p] += (uint32_t)tstart[p + 1] - tstart[p];
       __syncthreads();
     }
   }
 }
 
 // ------------------------------------------------------------------------ launchers
-size_t scatter_smem_bytes(int ksize, bool pairs, uint32_t B) {
+size_t scatter_smem_bytes(int ksize, bool pairs, uint32_t B, bool tree) {
   size_t off[9];
-  if (ksize == 4)
-    return pairs ? scatter_smem_layout<uint32_t, true>(B, off) : scatter_smem_layout<uint32_t, false>(B, off);
-  return pairs ? scatter_smem_layout<uint64_t, true>(B, off) : scatter_smem_layout<uint64_t, false>(B, off);
+#define AMS_SZ(K, P, T) return scatter_smem_layout<K, P, T>(B, off)
+  if (ksize == 4) {
+    if (pairs) { if (tree) AMS_SZ(uint32_t, true, true); else AMS_SZ(uint32_t, true, false); }
+    else { if (tree) AMS_SZ(uint32_t, false, true); else AMS_SZ(uint32_t, false, false); }
+  } else {
+    if (pairs) { if (tree) AMS_SZ(uint64_t, true, true); else AMS_SZ(uint64_t, true, false); }
+    else { if (tree) AMS_SZ(uint64_t, false, true); else AMS_SZ(uint64_t, false, false); }
+  }
+#undef AMS_SZ
 }
 
-static size_t classify_smem_bytes(int ksize, uint32_t B) {
+size_t classify_smem_bytes(int ksize, uint32_t B, bool tree) {
   uint32_t Bp = 1;
   while (Bp < B) Bp <<= 1;
-  return (size_t)2 * Bp * ksize + (size_t)(2 * B - 1) * 4;
+  const size_t cls = ksize == 4 ? cls_smem_bytes<uint32_t>(Bp, tree) : cls_smem_bytes<uint64_t>(Bp, tree);
+  return cls + (size_t)(2 * B - 1) * 4;
 }
 
 template <typename Kern>
@@ -335,17 +377,29 @@ static cudaError_t set_smem(Kern k, size_t bytes) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-cudaError_t launch_classify(const LevelArgs& a, int ksize, int grid, uint16_t* ids_out,
+cudaError_t launch_table(const LevelArgs& a, int ksize, int grid, cudaStream_t s) {
+  if (ksize == 4)
+    k_table<uint32_t><<<grid, 512, 0, s>>>(a);
+  else
+    k_table<uint64_t><<<grid, 512, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_classify(const LevelArgs& a, int ksize, bool tree, int grid, uint16_t* ids_out,
                             cudaStream_t s) {
-  const size_t sm = classify_smem_bytes(ksize, a.B);
+  const size_t sm = classify_smem_bytes(ksize, a.B, tree);
   cudaError_t e;
+#define AMS_LAUNCH_CLS(K, T)                                            \
+  do {                                                                  \
+    if ((e = set_smem(k_classify<K, T>, sm)) != cudaSuccess) return e;  \
+    k_classify<K, T><<<grid, 512, sm, s>>>(a, ids_out);                 \
+  } while (0)
   if (ksize == 4) {
-    if ((e = set_smem(k_classify<uint32_t>, sm)) != cudaSuccess) return e;
-    k_classify<uint32_t><<<grid, 512, sm, s>>>(a, ids_out);
+    if (tree) AMS_LAUNCH_CLS(uint32_t, true); else AMS_LAUNCH_CLS(uint32_t, false);
   } else {
-    if ((e = set_smem(k_classify<uint64_t>, sm)) != cudaSuccess) return e;
-    k_classify<uint64_t><<<grid, 512, sm, s>>>(a, ids_out);
+    if (tree) AMS_LAUNCH_CLS(uint64_t, true); else AMS_LAUNCH_CLS(uint64_t, false);
   }
+#undef AMS_LAUNCH_CLS
   return cudaGetLastError();
 }
 
@@ -354,18 +408,20 @@ cudaError_t launch_scan(const LevelArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_scatter(const LevelArgs& a, int ksize, bool pairs, int grid, cudaStream_t s) {
-  const size_t sm = scatter_smem_bytes(ksize, pairs, a.B);
+cudaError_t launch_scatter(const LevelArgs& a, int ksize, bool pairs, bool tree, int grid, cudaStream_t s) {
+  const size_t sm = scatter_smem_bytes(ksize, pairs, a.B, tree);
   cudaError_t e;
-#define AMS_LAUNCH_SCATTER(K, P)                                            \
+#define AMS_LAUNCH_SCATTER(K, P, T)                                         \
   do {                                                                      \
-    if ((e = set_smem(k_scatter<K, P>, sm)) != cudaSuccess) return e;       \
-    k_scatter<K, P><<<grid, 256, sm, s>>>(a);                               \
+    if ((e = set_smem(k_scatter<K, P, T>, sm)) != cudaSuccess) return e;    \
+    k_scatter<K, P, T><<<grid, 256, sm, s>>>(a);                            \
   } while (0)
   if (ksize == 4) {
-    if (pairs) AMS_LAUNCH_SCATTER(uint32_t, true); else AMS_LAUNCH_SCATTER(uint32_t, false);
+    if (pairs) { if (tree) AMS_LAUNCH_SCATTER(uint32_t, true, true); else AMS_LAUNCH_SCATTER(uint32_t, true, false); }
+    else { if (tree) AMS_LAUNCH_SCATTER(uint32_t, false, true); else AMS_LAUNCH_SCATTER(uint32_t, false, false); }
   } else {
-    if (pairs) AMS_LAUNCH_SCATTER(uint64_t, true); else AMS_LAUNCH_SCATTER(uint64_t, false);
+    if (pairs) { if (tree) AMS_LAUNCH_SCATTER(uint64_t, true, true); else AMS_LAUNCH_SCATTER(uint64_t, true, false); }
+    else { if (tree) AMS_LAUNCH_SCATTER(uint64_t, false, true); else AMS_LAUNCH_SCATTER(uint64_t, false, false); }
   }
 #undef AMS_LAUNCH_SCATTER
   return cudaGetLastError();

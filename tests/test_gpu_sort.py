@@ -101,6 +101,16 @@ def test_seed_and_parameters_do_not_change_the_output():
         assert same_bits(to_np(dk, np.uint64), exp), (levels, buckets, b, a, seed)
 
 
+@pytest.mark.parametrize("kt,bits,dist", [(O.KT_U64, 64, "uniform"), (O.KT_U64, 64, "zipf"),
+                                          (O.KT_U32, 32, "staggered"), (O.KT_F32, 32, None)])
+def test_tree_classifier_same_output(kt, bits, dist):
+    """The implicit-search-tree classifier (the paper's multisplitter) and the default
+    cell-table classifier give the same sort."""
+    keys = I.normal_f32(1 << 21, 8) if kt == O.KT_F32 else I.generate(dist, 1 << 21, 8, bits)
+    _sort_check(keys, kt, 2, [256, 256], seed=4, pairs=True, flags=ams.FLAG_TREE_CLASSIFIER)
+    _sort_check(keys, kt, 1, [1024], seed=5, flags=ams.FLAG_TREE_CLASSIFIER)
+
+
 def test_fallback_for_groups_above_capacity():
     """With two buckets per level and a tiny base-case capacity, some groups stay above
     capacity after the last level and take the global-memory merge path."""

@@ -308,6 +308,28 @@ def test_pieces_partition_and_cuts():
             assert not any(lo < b < hi for b in bounds)
 
 
+def test_piece_labels_agree_with_pieces():
+    """Delivery by piece: the labels group exactly the ids of each piece of
+    ``pieces`` (same positions, same final flags), in id order."""
+    rng = np.random.default_rng(18)
+    for trial in range(300):
+        B = int(rng.integers(2, 24))
+        cnt = rng.integers(0, 6, size=2 * B - 1)
+        cnt[1::2] = rng.choice([0, 1, 2, 9, 40], size=B - 1)
+        L, ends = O.bin_pack(cnt[0::2], int(rng.integers(1, B + 1)))
+        lab = O.piece_of_ids(cnt, B, L, ends)
+        assert np.all(np.diff(lab) >= 0) and lab[0] == 0
+        starts = np.concatenate([[0], np.cumsum(cnt)])
+        got = []
+        for v in np.unique(lab):
+            ids = np.nonzero(lab == v)[0]
+            b, e = int(starts[ids[0]]), int(starts[ids[-1] + 1])
+            fin = len(ids) == 1 and ids[0] % 2 == 1 and cnt[ids[0]] >= O.eq_cut_threshold(L)
+            if e > b:
+                got.append((b, e, int(fin)))
+        assert got == O.pieces(cnt, B, L, ends, 0)
+
+
 # ----------------------------------------------------------------- whole method
 @pytest.mark.parametrize("dist", I.DISTRIBUTIONS)
 def test_ams_restatement_equals_definition(dist):
