@@ -30,7 +30,7 @@ struct Plan {
   int ksize = 8;
   bool pairs = false;
   uint64_t n = 0, nseg_user = 1;
-  uint64_t seg1_cap = 0, bc0_cap = 0;
+  uint64_t seg1_cap = 0, bc0_cap = 0, big_cap = 0;
   LevelPlan lv[kMaxLevels];
 };
 
@@ -71,6 +71,7 @@ ams_status make_plan(uint64_t n, uint64_t nseg_user, ams_key_type kt, bool pairs
   const uint64_t big = n / (C + 1) + 1;  // segments larger than C that fit in n
   p->seg1_cap = std::min<uint64_t>(nseg_user, big);
   p->bc0_cap = std::min<uint64_t>(nseg_user, n) + 1;
+  p->big_cap = big;
   uint64_t nseg_cap = p->seg1_cap;
   const uint64_t chunk_goal = (n + (uint64_t)sm_count * 8 - 1) / ((uint64_t)sm_count * 8);
   for (int l = 0; l < p->L; ++l) {
@@ -131,6 +132,7 @@ struct Bufs {
   uint32_t* status;
   Seg* segs1;
   BcItem* bc0;
+  BcItem* big;
   LevelBufs lv[kMaxLevels];
 };
 
@@ -142,6 +144,7 @@ size_t carve(const Plan& p, char* base, Bufs* b) {
   b->vtmp = p.pairs ? c.take<uint64_t>(p.n) : nullptr;
   b->segs1 = c.take<Seg>(p.seg1_cap + 1);
   b->bc0 = c.take<BcItem>(p.bc0_cap);
+  b->big = c.take<BcItem>(p.big_cap + 1);
   for (int l = 0; l < p.L; ++l) {
     const LevelPlan& lp = p.lv[l];
     LevelBufs& lb = b->lv[l];
@@ -345,7 +348,8 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
   ba.out = rq->keys_out;
   ba.vout = rq->vals_out;
   auto run_basecase = [&](const void* src, const uint64_t* vsrc, const BcItem* items,
-                          const LevelCounters* ctr, int tf_load, uint64_t cap_items) -> ams_status {
+                          const uint32_t* nitems, int tf_load, uint64_t cap_items,
+                          bool big) -> ams_status {
     ba.src = src;
     ba.vsrc = vsrc;
     // the merge fallback ping-pongs between the output and the temporary buffer: an
@@ -354,16 +358,17 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
     ba.scratch = b.tmp;
     ba.vscratch = b.vtmp;
     ba.items = items;
-    ba.ctr = ctr;
+    ba.nitems = nitems;
     ba.tf_load = tf_load;
     ba.tf_store = f32 ? 1 : 0;
     ba.status = b.status;
     const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(cap_items, bc_grid_cap));
     ln.begin(AMS_K_BASECASE);
-    cudaError_t e = ln.end(launch_basecase(ba, p.ksize, p.pairs, grid, s));
+    cudaError_t e = ln.end(launch_basecase(ba, p.ksize, p.pairs, big, grid, s));
     return cuda_status(e);
   };
-  if ((st = run_basecase(rq->keys_in, rq->vals_in, b.bc0, &b.ctr[0], f32 ? 1 : 0, p.bc0_cap)) != AMS_OK)
+  if ((st = run_basecase(rq->keys_in, rq->vals_in, b.bc0, &b.ctr[0].n_bc, f32 ? 1 : 0, p.bc0_cap,
+                         false)) != AMS_OK)
     return st;
 
   LevelArgs la{};
@@ -423,6 +428,8 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
     la.items_cap = (uint32_t)std::min<uint64_t>(lp.items_cap, 0xFFFFFFFFull);
     la.next_cap = (uint32_t)lp.next_cap;
     la.bc_cap = (uint32_t)std::min<uint64_t>(lp.bc_cap, 0xFFFFFFFFull);
+    la.big = b.big;
+    la.big_cap = (uint32_t)p.big_cap;
     const int wide = SM * 4;
     const int seg_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(lp.nseg_cap, (uint64_t)SM * 2));
     ln.begin(AMS_K_SETUP);
@@ -443,7 +450,10 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
     AMS_TRY(ln.end(launch_binpack(la, seg_grid, s)));
     ln.begin(AMS_K_SCATTER);
     AMS_TRY(ln.end(launch_scatter(la, p.ksize, p.pairs, tree, SM * 2, s)));
-    if ((st = run_basecase(la.dst, la.vdst, lb.bc, &b.ctr[l], 0, lp.bc_cap)) != AMS_OK) return st;
+    if ((st = run_basecase(la.dst, la.vdst, lb.bc, &b.ctr[l].n_bc, 0, lp.bc_cap, false)) != AMS_OK)
+      return st;
+    if (la.last && (st = run_basecase(la.dst, la.vdst, b.big, &b.ctr[l].n_big, 0, p.big_cap, true)) != AMS_OK)
+      return st;
   }
   return AMS_OK;
 }
@@ -582,6 +592,8 @@ static LevelArgs step_level(Context* cx, const StepWs& w, uint32_t B, uint32_t a
   la.items_cap = 0xFFFFFFFFu;
   la.next_cap = 2 * la.nid + 16;
   la.bc_cap = 2 * la.nid + 16;
+  la.big = w.bc;   // step calls never leave a group above capacity (C is unbounded)
+  la.big_cap = 0;
   return la;
 }
 
@@ -962,11 +974,11 @@ ams_status ams_step_base_case(void* d_keys, uint64_t* d_vals, uint64_t n, ams_ke
   ba.vsrc = d_vals;
   ba.vout = d_vals;
   ba.items = w.bc;
-  ba.ctr = &w.ctr[1];
+  ba.nitems = &w.ctr[1].n_bc;
   ba.tf_load = kt == AMS_F32;
   ba.tf_store = kt == AMS_F32;
   ba.status = cx->d_status;
-  AMS_TRY(launch_basecase(ba, ks, d_vals != nullptr, 1, s));
+  AMS_TRY(launch_basecase(ba, ks, d_vals != nullptr, false, 1, s));
   return AMS_OK;
 }
 

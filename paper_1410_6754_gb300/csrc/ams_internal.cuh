@@ -59,7 +59,8 @@ struct LevelCounters {
   uint32_t tiles, pairs, items, samples, nseg;
   uint32_t keys;       // keys in this level's segments
   uint32_t bc_keys;    // keys in this level's base-case items
-  uint32_t pad[3];
+  uint32_t n_big;      // groups above capacity after the last level
+  uint32_t pad[2];
 };
 
 struct LevelArgs {
@@ -102,9 +103,10 @@ struct LevelArgs {
   uint32_t pieces_per_id;  // 1: every bucket is its own piece (step calls)
   Seg* segs_next;
   BcItem* bc;
+  BcItem* big;  // groups above capacity on the last level
   LevelCounters* ctr;
   uint32_t* status;
-  uint32_t nseg_cap, samples_cap, items_cap, next_cap, bc_cap;
+  uint32_t nseg_cap, samples_cap, items_cap, next_cap, bc_cap, big_cap;
 };
 
 struct InitArgs {
@@ -128,7 +130,7 @@ struct BaseArgs {
   uint64_t* vout;
   uint64_t* vscratch;
   const BcItem* items;
-  const LevelCounters* ctr;  // n_bc
+  const uint32_t* nitems;    // item count (a device counter)
   int tf_load;   // apply the float order map on load
   int tf_store;  // apply its inverse on store
   uint32_t* status;
@@ -211,7 +213,7 @@ cudaError_t launch_classify(const LevelArgs& a, int ksize, bool tree, int grid, 
 cudaError_t launch_scan(const LevelArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_binpack(const LevelArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_scatter(const LevelArgs& a, int ksize, bool pairs, bool tree, int grid, cudaStream_t s);
-cudaError_t launch_basecase(const BaseArgs& a, int ksize, bool pairs, int grid, cudaStream_t s);
+cudaError_t launch_basecase(const BaseArgs& a, int ksize, bool pairs, bool big, int grid, cudaStream_t s);
 
 // shared-memory bytes each kernel needs (for occupancy and opt-in)
 size_t scatter_smem_bytes(int ksize, bool pairs, uint32_t B, bool tree);

@@ -96,83 +96,102 @@ __device__ __forceinline__ T block_reduce_max(T v, T* ws) {
 }
 
 // Shared-memory arrays of the cell sort.  keys / pos hold up to `cap` elements,
-// cells up to `cap / 2` counters (at least 1).
+// cells up to `cap / 2 + 1` counters.
 template <typename K>
 struct CellSortSmem {
   K* keys;
   uint16_t* pos;
   uint32_t* cells;
-  K* red;        // NT/32 + 1 keys for reductions
+  K* red;        // 2 * (NT/32) keys for reductions
   uint32_t* ws;  // NT/32 + 1 words for scans
 };
 
 // Stable sort of m keys held in registers (element e = threadIdx.x + q*NT, q < KPT)
 // by (key, e).  For every element, emit(final_position, key, e) is called exactly
-// once.  Method: spread the keys over about m/2 equal-width cells of [min, max]
-// (counting by shared-memory atomics), then rank each key inside its cell by
-// comparing it with every other key of the cell, ties broken by e -- the all-pairs
-// ranking of Section 4.2 applied to the small cells.  All keys equal: identity.
+// once; slots are visited in a block-strided order, so consecutive threads emit
+// near-consecutive positions.  Method: spread the keys over about m/2 equal-width
+// cells of [min, max] (shared-memory atomics count the cells, a scan gives their
+// starts, a second atomic pass claims each key a slot in its cell), then rank each
+// key inside its cell by comparing it with every other key of the cell, ties broken
+// by e -- the all-pairs ranking of Section 4.2 applied to the small cells.  All keys
+// equal: identity.
 template <typename K, int NT, int KPT, typename Emit>
 __device__ __forceinline__ void cell_sort(const K (&x)[KPT], uint32_t m, uint32_t cap,
                                           const CellSortSmem<K>& sm, Emit emit) {
-  const uint32_t tid = threadIdx.x;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   K lo = key_max<K>(), hi = K(0);
 #pragma unroll
   for (int q = 0; q < KPT; ++q) {
-    uint32_t e = tid + q * NT;
-    if (e < m) {
+    if ((uint32_t)q * NT >= m) break;
+    if (tid + q * NT < m) {
       lo = x[q] < lo ? x[q] : lo;
       hi = x[q] > hi ? x[q] : hi;
     }
   }
-  const K kmin = block_reduce_min<NT, K>(lo, sm.red);
-  const K kmax = block_reduce_max<NT, K>(hi, sm.red);
+  // block min and max in one round
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const K a = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+    const K b = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+    lo = a < lo ? a : lo;
+    hi = b > hi ? b : hi;
+  }
+  if (lane == 0) {
+    sm.red[w] = lo;
+    sm.red[NT / 32 + w] = hi;
+  }
+  __syncthreads();
+  K kmin = sm.red[0], kmax = sm.red[NT / 32];
+#pragma unroll
+  for (int i = 1; i < NT / 32; ++i) {
+    kmin = sm.red[i] < kmin ? sm.red[i] : kmin;
+    kmax = sm.red[NT / 32 + i] > kmax ? sm.red[NT / 32 + i] : kmax;
+  }
   if (kmin == kmax) {
 #pragma unroll
     for (int q = 0; q < KPT; ++q) {
-      uint32_t e = tid + q * NT;
+      if ((uint32_t)q * NT >= m) break;
+      const uint32_t e = tid + q * NT;
       if (e < m) emit(e, x[q], e);
     }
     __syncthreads();
     return;
   }
-  // number of cells: power of two near m/2, at most cap/2
-  uint32_t want = (m + 1) / 2;
-  uint32_t lgM = want > 1 ? 32 - __clz((int)(want - 1)) : 0;
-  while ((1u << lgM) > max(1u, cap / 2)) --lgM;
+  // number of cells: power of two near m/2, at least 2 and at most cap/2
+  const uint32_t want = (m + 1) / 2;
+  uint32_t lgM = want > 2 ? 32 - __clz((int)(want - 1)) : 1;
+  while ((1u << lgM) > max(2u, cap / 2)) --lgM;
   const uint32_t M = 1u << lgM;
   const int nb = bitlen<K>((K)(kmax - kmin));
-  const int sh = nb > (int)lgM ? nb - (int)lgM : 0;
-  constexpr int kBits = 8 * sizeof(K);
-  auto cell_of = [&](K v) -> uint32_t {
-    return sh >= kBits ? 0u : (uint32_t)((K)(v - kmin) >> sh);
-  };
-  for (uint32_t c = tid; c < M; c += NT) sm.cells[c] = 0;
+  const int sh = nb > (int)lgM ? nb - (int)lgM : 0;  // below the key width as lgM >= 1
+  // cells[0] stays 0; cell c counts in cells[c+1], so that after the scan and the
+  // slot claims below cells[c] / cells[c+1] bound cell c
+  for (uint32_t c = tid; c <= M; c += NT) sm.cells[c] = 0;
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < KPT; ++q) {
-    uint32_t e = tid + q * NT;
-    if (e < m) atomicAdd(&sm.cells[cell_of(x[q])], 1u);
+    if ((uint32_t)q * NT >= m) break;
+    if (tid + q * NT < m) atomicAdd(&sm.cells[(uint32_t)((K)(x[q] - kmin) >> sh) + 1], 1u);
   }
   __syncthreads();
-  block_scan_array<NT, uint32_t>(sm.cells, M, sm.ws);
+  block_scan_array<NT, uint32_t>(sm.cells + 1, M, sm.ws);  // cells[c+1] = start of c
 #pragma unroll
   for (int q = 0; q < KPT; ++q) {
-    uint32_t e = tid + q * NT;
+    if ((uint32_t)q * NT >= m) break;
+    const uint32_t e = tid + q * NT;
     if (e < m) {
-      uint32_t s = atomicAdd(&sm.cells[cell_of(x[q])], 1u);
+      const uint32_t c = (uint32_t)((K)(x[q] - kmin) >> sh);
+      const uint32_t s = atomicAdd(&sm.cells[c + 1], 1u);  // afterwards: end of c
       sm.keys[s] = x[q];
       sm.pos[s] = (uint16_t)e;
     }
   }
   __syncthreads();
-  // cells[c] is now the end of cell c
   for (uint32_t s = tid; s < m; s += NT) {
     const K v = sm.keys[s];
     const uint32_t p = sm.pos[s];
-    const uint32_t c = cell_of(v);
-    const uint32_t b = c ? sm.cells[c - 1] : 0u;
-    const uint32_t en = sm.cells[c];
+    const uint32_t c = (uint32_t)((K)(v - kmin) >> sh);
+    const uint32_t b = sm.cells[c], en = sm.cells[c + 1];
     uint32_t r = 0;
     for (uint32_t t = b; t < en; ++t) {
       const K y = sm.keys[t];

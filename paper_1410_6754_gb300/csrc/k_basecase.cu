@@ -18,6 +18,8 @@ struct BaseCfg {
   static constexpr int NT = 512;
   static constexpr uint32_t CAP = (sizeof(K) == 4 && !PAIRS) ? 16384u : 8192u;
   static constexpr int KPT = CAP / NT;
+  // two blocks per SM when their shared memory fits (keys-only 64-bit keys)
+  static constexpr int MINB = (sizeof(K) == 8 && !PAIRS) ? 2 : 1;
 };
 
 template <typename K, bool PAIRS>
@@ -26,11 +28,22 @@ __host__ __device__ constexpr size_t base_smem_layout(size_t* off) {
   size_t o = 0;
   off[0] = o; o += (size_t)C::CAP * sizeof(K);         // keys
   off[1] = o; o += (size_t)C::CAP * 2;                 // pos
-  off[2] = o; o += (size_t)(C::CAP / 2) * 4;           // cells
-  off[3] = o; o += PAIRS ? (size_t)C::CAP * 8 : 0;     // payloads
-  off[4] = o; o += (size_t)(C::NT / 32 + 1) * sizeof(uint64_t);  // red
-  off[5] = o; o += (size_t)(C::NT / 32 + 1) * 4;       // ws
+  off[2] = o;                                          // (unused)
+  off[3] = o; o += (size_t)(C::CAP / 2 + 1) * 4;       // cells
+  o = (o + 15) & ~(size_t)15;
+  off[4] = o; o += PAIRS ? (size_t)C::CAP * 8 : 0;     // payloads
+  off[5] = o; o += (size_t)2 * (C::NT / 32) * sizeof(uint64_t);  // red
+  off[6] = o; o += (size_t)(C::NT / 32 + 1) * 4;       // ws
   return o;
+}
+
+template <typename K, bool PAIRS>
+__device__ __forceinline__ CellSortSmem<K> base_smem(unsigned char* smem, uint64_t** vals_s) {
+  size_t off[7];
+  base_smem_layout<K, PAIRS>(off);
+  *vals_s = (uint64_t*)(smem + off[4]);
+  return CellSortSmem<K>{(K*)(smem + off[0]), (uint16_t*)(smem + off[1]), (uint32_t*)(smem + off[3]),
+                         (K*)(smem + off[5]), (uint32_t*)(smem + off[6])};
 }
 
 // Sort keys [b, b+m) of `src` (m <= CAP) and write them to `dst` at the same
@@ -43,10 +56,12 @@ __device__ __forceinline__ void sort_block(const K* src, K* dst, const uint64_t*
   K x[C::KPT];
 #pragma unroll
   for (int q = 0; q < C::KPT; ++q) {
+    x[q] = K(0);
+    if ((uint32_t)q * C::NT >= m) break;  // the rest of the block's slots are empty
     const uint32_t e = threadIdx.x + q * C::NT;
-    x[q] = e < m ? order_in<K>(src[b + e], tf_in) : K(0);
-    if constexpr (PAIRS) {
-      if (e < m) vals_s[e] = vsrc[b + e];
+    if (e < m) {
+      x[q] = order_in<K>(src[b + e], tf_in);
+      if constexpr (PAIRS) vals_s[e] = vsrc[b + e];
     }
   }
   __syncthreads();  // every load done before any store (src may equal dst)
@@ -109,15 +124,12 @@ __device__ void big_sort(const BaseArgs& a, uint32_t b, uint32_t m, const CellSo
 }
 
 template <typename K, bool PAIRS>
-__global__ void __launch_bounds__(512) k_basecase(BaseArgs a) {
+__global__ void __launch_bounds__(512, BaseCfg<K, PAIRS>::MINB) k_basecase(BaseArgs a) {
   using C = BaseCfg<K, PAIRS>;
   extern __shared__ __align__(16) unsigned char smem[];
-  size_t off[6];
-  base_smem_layout<K, PAIRS>(off);
-  const CellSortSmem<K> sm{(K*)(smem + off[0]), (uint16_t*)(smem + off[1]), (uint32_t*)(smem + off[2]),
-                           (K*)(smem + off[4]), (uint32_t*)(smem + off[5])};
-  uint64_t* vals_s = (uint64_t*)(smem + off[3]);
-  const uint32_t nitems = a.ctr->n_bc;
+  uint64_t* vals_s;
+  const CellSortSmem<K> sm = base_smem<K, PAIRS>(smem, &vals_s);
+  const uint32_t nitems = *a.nitems;
   const K* src = (const K*)a.src;
   K* out = (K*)a.out;
   for (uint32_t it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -130,15 +142,28 @@ __global__ void __launch_bounds__(512) k_basecase(BaseArgs a) {
       }
     } else if (m <= C::CAP) {
       sort_block<K, PAIRS>(src, out, a.vsrc, a.vout, b, m, a.tf_load, a.tf_store, sm, vals_s);
-    } else {
-      big_sort<K, PAIRS>(a, b, m, sm, vals_s);
     }
     __syncthreads();
   }
 }
 
+// Groups still larger than the block capacity after the last level (BC_BIG items,
+// kept in their own list so that the hot kernel above stays small).
+template <typename K, bool PAIRS>
+__global__ void __launch_bounds__(512) k_bigsort(BaseArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* vals_s;
+  const CellSortSmem<K> sm = base_smem<K, PAIRS>(smem, &vals_s);
+  const uint32_t nitems = *a.nitems;
+  for (uint32_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BcItem item = a.items[it];
+    big_sort<K, PAIRS>(a, item.begin, item.end - item.begin, sm, vals_s);
+    __syncthreads();
+  }
+}
+
 size_t basecase_smem_bytes(int ksize, bool pairs) {
-  size_t off[6];
+  size_t off[7];
   if (ksize == 4) return pairs ? base_smem_layout<uint32_t, true>(off) : base_smem_layout<uint32_t, false>(off);
   return pairs ? base_smem_layout<uint64_t, true>(off) : base_smem_layout<uint64_t, false>(off);
 }
@@ -148,15 +173,22 @@ uint32_t basecase_max_cap(int ksize, bool pairs) {
   return pairs ? BaseCfg<uint64_t, true>::CAP : BaseCfg<uint64_t, false>::CAP;
 }
 
-cudaError_t launch_basecase(const BaseArgs& a, int ksize, bool pairs, int grid, cudaStream_t s) {
+cudaError_t launch_basecase(const BaseArgs& a, int ksize, bool pairs, bool big, int grid, cudaStream_t s) {
   const size_t sm = basecase_smem_bytes(ksize, pairs);
   cudaError_t e;
-#define AMS_LAUNCH_BASE(K, P)                                                              \
-  do {                                                                                     \
-    e = cudaFuncSetAttribute(k_basecase<K, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             (int)sm);                                                     \
-    if (e != cudaSuccess) return e;                                                        \
-    k_basecase<K, P><<<grid, 512, sm, s>>>(a);                                             \
+#define AMS_LAUNCH_BASE(K, P)                                                                  \
+  do {                                                                                         \
+    if (big) {                                                                                 \
+      e = cudaFuncSetAttribute(k_bigsort<K, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                               (int)sm);                                                       \
+      if (e != cudaSuccess) return e;                                                          \
+      k_bigsort<K, P><<<grid, 512, sm, s>>>(a);                                                \
+    } else {                                                                                   \
+      e = cudaFuncSetAttribute(k_basecase<K, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                               (int)sm);                                                       \
+      if (e != cudaSuccess) return e;                                                          \
+      k_basecase<K, P><<<grid, 512, sm, s>>>(a);                                               \
+    }                                                                                          \
   } while (0)
   if (ksize == 4) {
     if (pairs) AMS_LAUNCH_BASE(uint32_t, true); else AMS_LAUNCH_BASE(uint32_t, false);
@@ -192,11 +224,8 @@ __global__ void __launch_bounds__(512) k_sort_noalloc(void* keys, uint64_t* vals
                                                       uint64_t* scratch) {
   using C = BaseCfg<K, PAIRS>;
   extern __shared__ __align__(16) unsigned char smem[];
-  size_t off[6];
-  base_smem_layout<K, PAIRS>(off);
-  const CellSortSmem<K> sm{(K*)(smem + off[0]), (uint16_t*)(smem + off[1]), (uint32_t*)(smem + off[2]),
-                           (K*)(smem + off[4]), (uint32_t*)(smem + off[5])};
-  uint64_t* vals_s = (uint64_t*)(smem + off[3]);
+  uint64_t* vals_s;
+  const CellSortSmem<K> sm = base_smem<K, PAIRS>(smem, &vals_s);
   if (n <= C::CAP) {
     sort_block<K, PAIRS>((const K*)keys, (K*)keys, vals, vals, 0, n, tf, tf, sm, vals_s);
     return;

@@ -106,7 +106,12 @@ struct Emitter {
         atomicOr(a->status, ST_OVERFLOW);
       }
     } else {
-      push_bc(b, e, BC_BIG);
+      const uint32_t i = atomicAdd(&a->ctr->n_big, 1u);
+      if (i < a->big_cap) {
+        a->big[i] = BcItem{seg_begin + b, seg_begin + e, BC_BIG, 0};
+      } else {
+        atomicOr(a->status, ST_OVERFLOW);
+      }
     }
   }
 };

@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(512) k_table(LevelArgs a) {
 }
 
 // ------------------------------------------------------------------------- classify
-template <typename K, bool TREE>
+template <typename K, bool TREE, bool IDS>
 __global__ void __launch_bounds__(512) k_classify(LevelArgs a, uint16_t* ids_out) {
   constexpr int NT = 512;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -80,8 +80,6 @@ __global__ void __launch_bounds__(512) k_classify(LevelArgs a, uint16_t* ids_out
   const uint32_t nseg = a.ctr->nseg;
   const uint32_t items = a.ctr->items;
   const K* src = (const K*)a.src;
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t wbase = threadIdx.x & ~31u;
   uint32_t cur_g = 0xFFFFFFFFu;
   for (uint32_t k = blockIdx.x; k < items; k += gridDim.x) {
     const uint32_t g = find_seg<&SegInfo::item_off>(a.sinfo, nseg, k);
@@ -104,35 +102,48 @@ __global__ void __launch_bounds__(512) k_classify(LevelArgs a, uint16_t* ids_out
     const uint32_t b0 = min(lo + head, hi);
     const uint32_t nv = (hi - b0) / V;
     const uint32_t b1 = b0 + nv * V;
-    auto put = [&](uint32_t pos, K x, bool valid) {
-      const uint32_t id = valid ? classify<K>(cs, TREE, a.logBp, a.B, order_in<K>(x, a.tf_src)) : 0xFFFFFFFFu;
-      // a warp whose keys all share one bucket adds them with one atomic
-      const uint32_t id0 = __shfl_sync(0xFFFFFFFFu, id, 0);
-      const uint32_t vm = __ballot_sync(0xFFFFFFFFu, valid);
-      if (__all_sync(0xFFFFFFFFu, !valid || id == id0)) {
-        if (lane == 0 && vm) atomicAdd(&hist[id0], (uint32_t)__popc(vm));
-      } else if (valid) {
-        atomicAdd(&hist[id], 1u);
+    // per-thread run-length counting: one shared atomic whenever the bucket changes
+    // (sorted or duplicate-heavy input adds whole runs at once)
+    uint32_t run_id = 0xFFFFFFFFu, run_n = 0;
+    auto put = [&](uint32_t pos, K x) {
+      const uint32_t id = classify<K>(cs, TREE, a.logBp, a.B, order_in<K>(x, a.tf_src));
+      if (id != run_id) {
+        if (run_n) atomicAdd(&hist[run_id], run_n);
+        run_id = id;
+        run_n = 0;
       }
-      if (ids_out && valid) ids_out[pos - a.segs[0].begin] = (uint16_t)id;
+      ++run_n;
+      if constexpr (IDS) ids_out[pos - a.segs[0].begin] = (uint16_t)id;
     };
     const uint32_t nscalar = (b0 - lo) + (hi - b1);
-    for (uint32_t wb = wbase; wb < nscalar; wb += NT) {
-      const uint32_t e = wb + lane;
-      const bool valid = e < nscalar;
+    for (uint32_t e = threadIdx.x; e < nscalar; e += NT) {
       const uint32_t pos = e < (b0 - lo) ? lo + e : b1 + (e - (b0 - lo));
-      put(pos, valid ? src[pos] : K(0), valid);
+      put(pos, src[pos]);
     }
+    // four 128-bit loads in flight per thread
     const uint4* vp = (const uint4*)(src + b0);
-    for (uint32_t wb = wbase; wb < nv; wb += NT) {
-      const uint32_t v = wb + lane;
-      const bool valid = v < nv;
-      uint4 w = valid ? __ldcs(vp + v) : make_uint4(0, 0, 0, 0);
+    constexpr uint32_t U = 4;
+    uint32_t v = threadIdx.x;
+    for (; v + (U - 1) * NT < nv; v += U * NT) {
+      uint4 w[U];
+#pragma unroll
+      for (uint32_t u = 0; u < U; ++u) w[u] = __ldcs(vp + v + u * NT);
+#pragma unroll
+      for (uint32_t u = 0; u < U; ++u) {
+        K ks[V];
+        memcpy(ks, &w[u], 16);
+#pragma unroll
+        for (uint32_t e = 0; e < V; ++e) put(b0 + (v + u * NT) * V + e, ks[e]);
+      }
+    }
+    for (; v < nv; v += NT) {
+      const uint4 w = __ldcs(vp + v);
       K ks[V];
       memcpy(ks, &w, 16);
 #pragma unroll
-      for (uint32_t e = 0; e < V; ++e) put(b0 + v * V + e, ks[e], valid);
+      for (uint32_t e = 0; e < V; ++e) put(b0 + v * V + e, ks[e]);
     }
+    if (run_n) atomicAdd(&hist[run_id], run_n);
     __syncthreads();
     uint32_t* out = a.counts + (size_t)k * a.nid;
     for (uint32_t i = threadIdx.x; i < a.nid; i += NT) out[i] = hist[i];
@@ -267,7 +278,12 @@ __global__ void __launch_bounds__(256) k_scatter(LevelArgs a) {
 
     for (uint32_t t0 = lo; t0 < hi; t0 += TILE) {
       const uint32_t tn = min((uint32_t)TILE, hi - t0);
-      for (uint32_t i = tid; i < (uint32_t)Cfg::W * S / 2; i += NT) ((uint32_t*)cnt)[i] = 0;
+      {
+        // counters of pieces 0..P (P = the dummy piece of the tile's empty slots)
+        const uint32_t hw = (P + 2) / 2;  // 32-bit words per warp row
+        for (uint32_t i = tid; i < (uint32_t)Cfg::W * hw; i += NT)
+          ((uint32_t*)(cnt + (i / hw) * S))[i % hw] = 0;
+      }
       // 1. load, classify, rank among the warp's keys of the same piece
       K x[R];
       uint64_t v[PAIRS ? R : 1];
@@ -389,10 +405,15 @@ cudaError_t launch_classify(const LevelArgs& a, int ksize, bool tree, int grid, 
                             cudaStream_t s) {
   const size_t sm = classify_smem_bytes(ksize, a.B, tree);
   cudaError_t e;
-#define AMS_LAUNCH_CLS(K, T)                                            \
-  do {                                                                  \
-    if ((e = set_smem(k_classify<K, T>, sm)) != cudaSuccess) return e;  \
-    k_classify<K, T><<<grid, 512, sm, s>>>(a, ids_out);                 \
+#define AMS_LAUNCH_CLS(K, T)                                                      \
+  do {                                                                            \
+    if (ids_out) {                                                                \
+      if ((e = set_smem(k_classify<K, T, true>, sm)) != cudaSuccess) return e;    \
+      k_classify<K, T, true><<<grid, 512, sm, s>>>(a, ids_out);                   \
+    } else {                                                                      \
+      if ((e = set_smem(k_classify<K, T, false>, sm)) != cudaSuccess) return e;   \
+      k_classify<K, T, false><<<grid, 512, sm, s>>>(a, ids_out);                  \
+    }                                                                             \
   } while (0)
   if (ksize == 4) {
     if (tree) AMS_LAUNCH_CLS(uint32_t, true); else AMS_LAUNCH_CLS(uint32_t, false);

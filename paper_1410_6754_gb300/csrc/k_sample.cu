@@ -100,8 +100,8 @@ __global__ void __launch_bounds__(512) k_sample_sort(LevelArgs a, K* raw_out, co
   constexpr int NT = 512, KPT = kSampleTile / NT;
   __shared__ K keys_s[kSampleTile];
   __shared__ uint16_t pos_s[kSampleTile];
-  __shared__ uint32_t cells_s[kSampleTile / 2];
-  __shared__ K red_s[NT / 32 + 1];
+  __shared__ uint32_t cells_s[kSampleTile / 2 + 1];
+  __shared__ K red_s[2 * (NT / 32)];
   __shared__ uint32_t ws_s[NT / 32 + 1];
   const CellSortSmem<K> sm{keys_s, pos_s, cells_s, red_s, ws_s};
   const uint32_t nseg = a.ctr->nseg;
