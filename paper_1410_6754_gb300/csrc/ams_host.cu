@@ -133,6 +133,7 @@ struct Bufs {
   Seg* segs1;
   BcItem* bc0;
   BcItem* big;
+  uint16_t* ids;  // bucket id of every key (rewritten by each level)
   LevelBufs lv[kMaxLevels];
 };
 
@@ -141,6 +142,7 @@ size_t carve(const Plan& p, char* base, Bufs* b) {
   b->status = c.take<uint32_t>(64);
   b->ctr = c.take<LevelCounters>(kMaxLevels + 1);
   b->tmp = c.take<char>(p.n * p.ksize);
+  b->ids = c.take<uint16_t>(p.n);
   b->vtmp = p.pairs ? c.take<uint64_t>(p.n) : nullptr;
   b->segs1 = c.take<Seg>(p.seg1_cap + 1);
   b->bc0 = c.take<BcItem>(p.bc0_cap);
@@ -422,6 +424,7 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
     la.piece_of = lb.piece_of;
     la.piece_start = lb.piece_start;
     la.npieces = lb.npieces;
+    la.ids = b.ids;
     la.pieces_per_id = 0;
     la.nseg_cap = (uint32_t)lp.nseg_cap;
     la.samples_cap = (uint32_t)std::min<uint64_t>(lp.samples_cap, 0xFFFFFFFFull);
@@ -443,13 +446,13 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
     ln.begin(AMS_K_TABLE);
     AMS_TRY(ln.end(launch_table(la, p.ksize, seg_grid, s)));
     ln.begin(AMS_K_CLASSIFY);
-    AMS_TRY(ln.end(launch_classify(la, p.ksize, tree, SM * 4, nullptr, s)));
+    AMS_TRY(ln.end(launch_classify(la, p.ksize, tree, SM * 4, s)));
     ln.begin(AMS_K_SCAN);
     AMS_TRY(ln.end(launch_scan(la, SM * 8, s)));
     ln.begin(AMS_K_BINPACK);
     AMS_TRY(ln.end(launch_binpack(la, seg_grid, s)));
     ln.begin(AMS_K_SCATTER);
-    AMS_TRY(ln.end(launch_scatter(la, p.ksize, p.pairs, tree, SM * 2, s)));
+    AMS_TRY(ln.end(launch_scatter(la, p.ksize, p.pairs, SM * 2, s)));
     if ((st = run_basecase(la.dst, la.vdst, lb.bc, &b.ctr[l].n_bc, 0, lp.bc_cap, false)) != AMS_OK)
       return st;
     if (la.last && (st = run_basecase(la.dst, la.vdst, b.big, &b.ctr[l].n_big, 0, p.big_cap, true)) != AMS_OK)
@@ -487,6 +490,7 @@ struct StepWs {
   uint16_t* piece_of;
   uint32_t* piece_start;
   uint32_t* npieces;
+  uint16_t* ids;
 };
 
 __global__ void k_step_prepare(Seg* segs, LevelCounters* ctr, uint32_t begin, uint32_t end,
@@ -541,6 +545,7 @@ static ams_status step_ws(Context* cx, uint64_t samples, uint32_t B, uint64_t it
     w->piece_of = c.take<uint16_t>(nid + 1);
     w->piece_start = c.take<uint32_t>(nid + 1);
     w->npieces = c.take<uint32_t>(1);
+    w->ids = c.take<uint16_t>(items * 8192);  // covers n keys: items > n / 8192
     return c.off + 256;
   };
   const size_t need = lay(nullptr);
@@ -585,6 +590,7 @@ static LevelArgs step_level(Context* cx, const StepWs& w, uint32_t B, uint32_t a
   la.piece_of = w.piece_of;
   la.piece_start = w.piece_start;
   la.npieces = w.npieces;
+  la.ids = w.ids;
   la.pieces_per_id = 0;
   la.status = cx->d_status;
   la.nseg_cap = 1;
@@ -890,7 +896,8 @@ ams_status ams_step_classify(const void* d_keys, uint64_t n, ams_key_type kt, co
   AMS_TRY(cudaGetLastError());
   AMS_TRY(launch_setup(la, s));
   AMS_TRY(launch_table(la, ks, 1, s));
-  AMS_TRY(launch_classify(la, ks, false, cx->sm_count * 4, d_ids, s));
+  if (d_ids) la.ids = d_ids;
+  AMS_TRY(launch_classify(la, ks, false, cx->sm_count * 4, s));
   AMS_TRY(launch_scan(la, cx->sm_count * 8, s));
   AMS_TRY(cudaMemcpyAsync(d_counts, w.totals, (size_t)la.nid * 4, cudaMemcpyDeviceToDevice, s));
   return AMS_OK;
@@ -948,10 +955,10 @@ ams_status ams_step_partition(const void* d_in, void* d_out, const uint64_t* d_v
   AMS_TRY(launch_setup(la, s));
   la.pieces_per_id = 1;  // deliver bucket by bucket
   AMS_TRY(launch_table(la, ks, 1, s));
-  AMS_TRY(launch_classify(la, ks, false, cx->sm_count * 4, nullptr, s));
+  AMS_TRY(launch_classify(la, ks, false, cx->sm_count * 4, s));
   AMS_TRY(launch_scan(la, cx->sm_count * 8, s));
   AMS_TRY(launch_binpack(la, 1, s));
-  AMS_TRY(launch_scatter(la, ks, d_vals_in != nullptr, false, cx->sm_count * 2, s));
+  AMS_TRY(launch_scatter(la, ks, d_vals_in != nullptr, cx->sm_count * 2, s));
   return AMS_OK;
 }
 

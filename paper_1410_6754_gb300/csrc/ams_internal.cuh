@@ -101,6 +101,7 @@ struct LevelArgs {
   uint32_t* piece_start; // per segment x piece: first position (relative)
   uint32_t* npieces;     // per segment: number of pieces
   uint32_t pieces_per_id;  // 1: every bucket is its own piece (step calls)
+  uint16_t* ids;           // bucket id of every key of the level, by position
   Seg* segs_next;
   BcItem* bc;
   BcItem* big;  // groups above capacity on the last level
@@ -208,15 +209,14 @@ cudaError_t launch_sample_sort(const LevelArgs& a, int ksize, int grid, cudaStre
 cudaError_t launch_cross_rank(const LevelArgs& a, int ksize, int grid, cudaStream_t s);
 cudaError_t launch_splitters(const LevelArgs& a, int ksize, int grid, cudaStream_t s);
 cudaError_t launch_table(const LevelArgs& a, int ksize, int grid, cudaStream_t s);
-cudaError_t launch_classify(const LevelArgs& a, int ksize, bool tree, int grid, uint16_t* ids_out,
-                            cudaStream_t s);
+cudaError_t launch_classify(const LevelArgs& a, int ksize, bool tree, int grid, cudaStream_t s);
 cudaError_t launch_scan(const LevelArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_binpack(const LevelArgs& a, int grid, cudaStream_t s);
-cudaError_t launch_scatter(const LevelArgs& a, int ksize, bool pairs, bool tree, int grid, cudaStream_t s);
+cudaError_t launch_scatter(const LevelArgs& a, int ksize, bool pairs, int grid, cudaStream_t s);
 cudaError_t launch_basecase(const BaseArgs& a, int ksize, bool pairs, bool big, int grid, cudaStream_t s);
 
 // shared-memory bytes each kernel needs (for occupancy and opt-in)
-size_t scatter_smem_bytes(int ksize, bool pairs, uint32_t B, bool tree);
+size_t scatter_smem_bytes(int ksize, bool pairs, uint32_t B);
 size_t classify_smem_bytes(int ksize, uint32_t B, bool tree);
 size_t basecase_smem_bytes(int ksize, bool pairs);
 uint32_t basecase_max_cap(int ksize, bool pairs);

@@ -1,7 +1,8 @@
 // Partitioning and delivery of one distribution level (Section 6; equality buckets of
 // Appendix D; prefix-sum delivery of Section 4.3):
 //   table     per segment: the cell table of the table classifier (classifier.cuh)
-//   classify  every key of a chunk gets its bucket id; per-chunk bucket counts
+//   classify  every key of a chunk gets its bucket id (stored, 16 bits per key, for
+//             the scatter); per-chunk bucket counts
 //   scan      per (segment, id): exclusive prefix of the counts over the segment's
 //             chunks, and the bucket totals
 //   scatter   group-wise delivery: every key goes to its *piece* (a run of buckets of
@@ -69,8 +70,8 @@ __global__ void __launch_bounds__(512) k_table(LevelArgs a) {
 }
 
 // ------------------------------------------------------------------------- classify
-template <typename K, bool TREE, bool IDS>
-__global__ void __launch_bounds__(512) k_classify(LevelArgs a, uint16_t* ids_out) {
+template <typename K, bool TREE>
+__global__ void __launch_bounds__(512) k_classify(LevelArgs a) {
   constexpr int NT = 512;
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t Bp = 1u << a.logBp;
@@ -80,6 +81,7 @@ __global__ void __launch_bounds__(512) k_classify(LevelArgs a, uint16_t* ids_out
   const uint32_t nseg = a.ctr->nseg;
   const uint32_t items = a.ctr->items;
   const K* src = (const K*)a.src;
+  uint16_t* ids = a.ids;
   uint32_t cur_g = 0xFFFFFFFFu;
   for (uint32_t k = blockIdx.x; k < items; k += gridDim.x) {
     const uint32_t g = find_seg<&SegInfo::item_off>(a.sinfo, nseg, k);
@@ -102,23 +104,48 @@ __global__ void __launch_bounds__(512) k_classify(LevelArgs a, uint16_t* ids_out
     const uint32_t b0 = min(lo + head, hi);
     const uint32_t nv = (hi - b0) / V;
     const uint32_t b1 = b0 + nv * V;
+    // the ids of one 128-bit key vector are stored together when that is aligned
+    const bool ids_vec = ((uintptr_t)(ids + b0) % (2 * V)) == 0;
     // per-thread run-length counting: one shared atomic whenever the bucket changes
     // (sorted or duplicate-heavy input adds whole runs at once)
     uint32_t run_id = 0xFFFFFFFFu, run_n = 0;
-    auto put = [&](uint32_t pos, K x) {
-      const uint32_t id = classify<K>(cs, TREE, a.logBp, a.B, order_in<K>(x, a.tf_src));
+    auto count = [&](uint32_t id) {
       if (id != run_id) {
         if (run_n) atomicAdd(&hist[run_id], run_n);
         run_id = id;
         run_n = 0;
       }
       ++run_n;
-      if constexpr (IDS) ids_out[pos - a.segs[0].begin] = (uint16_t)id;
+    };
+    auto cls = [&](K x) { return classify<K>(cs, TREE, a.logBp, a.B, order_in<K>(x, a.tf_src)); };
+    auto vec = [&](uint32_t v, const uint4& w) {
+      K ks[V];
+      memcpy(ks, &w, 16);
+      uint16_t id[V];
+#pragma unroll
+      for (uint32_t e = 0; e < V; ++e) {
+        id[e] = (uint16_t)cls(ks[e]);
+        count(id[e]);
+      }
+      const uint32_t p = b0 + v * V;
+      if (ids_vec) {
+        if constexpr (V == 2) {
+          *(uint32_t*)(ids + p) = (uint32_t)id[0] | ((uint32_t)id[1] << 16);
+        } else {
+          *(uint2*)(ids + p) = make_uint2((uint32_t)id[0] | ((uint32_t)id[1] << 16),
+                                          (uint32_t)id[2] | ((uint32_t)id[3] << 16));
+        }
+      } else {
+#pragma unroll
+        for (uint32_t e = 0; e < V; ++e) ids[p + e] = id[e];
+      }
     };
     const uint32_t nscalar = (b0 - lo) + (hi - b1);
     for (uint32_t e = threadIdx.x; e < nscalar; e += NT) {
       const uint32_t pos = e < (b0 - lo) ? lo + e : b1 + (e - (b0 - lo));
-      put(pos, src[pos]);
+      const uint32_t id = cls(src[pos]);
+      count(id);
+      ids[pos] = (uint16_t)id;
     }
     // four 128-bit loads in flight per thread
     const uint4* vp = (const uint4*)(src + b0);
@@ -129,20 +156,9 @@ __global__ void __launch_bounds__(512) k_classify(LevelArgs a, uint16_t* ids_out
 #pragma unroll
       for (uint32_t u = 0; u < U; ++u) w[u] = __ldcs(vp + v + u * NT);
 #pragma unroll
-      for (uint32_t u = 0; u < U; ++u) {
-        K ks[V];
-        memcpy(ks, &w[u], 16);
-#pragma unroll
-        for (uint32_t e = 0; e < V; ++e) put(b0 + (v + u * NT) * V + e, ks[e]);
-      }
+      for (uint32_t u = 0; u < U; ++u) vec(v + u * NT, w[u]);
     }
-    for (; v < nv; v += NT) {
-      const uint4 w = __ldcs(vp + v);
-      K ks[V];
-      memcpy(ks, &w, 16);
-#pragma unroll
-      for (uint32_t e = 0; e < V; ++e) put(b0 + v * V + e, ks[e]);
-    }
+    for (; v < nv; v += NT) vec(v, __ldcs(vp + v));
     if (run_n) atomicAdd(&hist[run_id], run_n);
     __syncthreads();
     uint32_t* out = a.counts + (size_t)k * a.nid;
@@ -185,7 +201,8 @@ __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
 
 // -------------------------------------------------------------------------- scatter
 // Block of 256 threads = 8 warps; warp w owns keys [w*32R, (w+1)*32R) of a tile of
-// 256R keys; lane l of round q holds key w*32R + 32q + l.
+// 256R keys; lane l of round q holds key w*32R + 32q + l.  The bucket ids come from
+// the classify pass.
 template <typename K, bool PAIRS>
 struct ScatterCfg {
   static constexpr int NT = 256;
@@ -194,55 +211,50 @@ struct ScatterCfg {
   static constexpr int TILE = NT * R;
 };
 
-template <typename K, bool PAIRS, bool TREE>
+template <typename K, bool PAIRS>
 __host__ __device__ constexpr size_t scatter_smem_layout(uint32_t B, size_t* off) {
-  // offsets: classifier, piece_of, cnt, tstart, run_off, stage_key, stage_id, stage_val, ws
+  // offsets: piece_of, cnt, tstart, dbase, stage_key, stage_dst, stage_val, ws
   using C = ScatterCfg<K, PAIRS>;
-  uint32_t Bp = 1;
-  while (Bp < B) Bp <<= 1;
   const uint32_t nid = 2 * B - 1;
   const uint32_t S = (nid + 2) & ~1u;  // counter row stride (entries)
   size_t o = 0;
-  off[0] = o; o += cls_smem_bytes<K>(Bp, TREE);
-  off[1] = o; o += (size_t)nid * 2;
+  off[0] = o; o += (size_t)nid * 2;
   o = (o + 15) & ~(size_t)15;
-  off[2] = o; o += (size_t)C::W * S * 2;
-  off[3] = o; o += (size_t)(nid + 2) * 2;
+  off[1] = o; o += (size_t)C::W * S * 2;
+  off[2] = o; o += (size_t)(nid + 2) * 2;
   o = (o + 15) & ~(size_t)15;
-  off[4] = o; o += (size_t)nid * 4;
+  off[3] = o; o += (size_t)nid * 4;
   o = (o + 15) & ~(size_t)15;
-  off[5] = o; o += (size_t)C::TILE * sizeof(K);
-  off[6] = o; o += (size_t)C::TILE * 2;
+  off[4] = o; o += (size_t)C::TILE * sizeof(K);
+  off[5] = o; o += (size_t)C::TILE * 4;
   o = (o + 15) & ~(size_t)15;
-  off[7] = o; o += PAIRS ? (size_t)C::TILE * 8 : 0;
-  off[8] = o; o += 64 * 4;
+  off[6] = o; o += PAIRS ? (size_t)C::TILE * 8 : 0;
+  off[7] = o; o += 64 * 4;
   return o;
 }
 
-template <typename K, bool PAIRS, bool TREE>
+template <typename K, bool PAIRS>
 __global__ void __launch_bounds__(256) k_scatter(LevelArgs a) {
   using Cfg = ScatterCfg<K, PAIRS>;
   constexpr int NT = Cfg::NT, R = Cfg::R, TILE = Cfg::TILE;
   extern __shared__ __align__(16) unsigned char smem[];
-  size_t off[9];
-  scatter_smem_layout<K, PAIRS, TREE>(a.B, off);
-  const uint32_t Bp = 1u << a.logBp;
+  size_t off[8];
+  scatter_smem_layout<K, PAIRS>(a.B, off);
   const uint32_t nid = a.nid;
   const uint32_t S = (nid + 2) & ~1u;
-  ClsSmem<K> cs;
-  cls_bind<K>(cs, smem + off[0], Bp, TREE);
-  uint16_t* piece_of = (uint16_t*)(smem + off[1]);
-  uint16_t* cnt = (uint16_t*)(smem + off[2]);
-  uint16_t* tstart = (uint16_t*)(smem + off[3]);
-  uint32_t* run_off = (uint32_t*)(smem + off[4]);
-  K* stage_key = (K*)(smem + off[5]);
-  uint16_t* stage_id = (uint16_t*)(smem + off[6]);
-  uint64_t* stage_val = (uint64_t*)(smem + off[7]);
-  uint32_t* ws = (uint32_t*)(smem + off[8]);
+  uint16_t* piece_of = (uint16_t*)(smem + off[0]);
+  uint16_t* cnt = (uint16_t*)(smem + off[1]);
+  uint16_t* tstart = (uint16_t*)(smem + off[2]);
+  uint32_t* dbase = (uint32_t*)(smem + off[3]);  // run offset of each piece
+  K* stage_key = (K*)(smem + off[4]);
+  uint32_t* stage_dst = (uint32_t*)(smem + off[5]);
+  uint64_t* stage_val = (uint64_t*)(smem + off[6]);
+  uint32_t* ws = (uint32_t*)(smem + off[7]);
 
   const uint32_t nseg = a.ctr->nseg;
   const uint32_t items = a.ctr->items;
   const K* src = (const K*)a.src;
+  const uint16_t* ids = a.ids;
   K* dst = (K*)a.dst;
   const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const uint32_t ltm = lanemask_lt();
@@ -257,20 +269,18 @@ __global__ void __launch_bounds__(256) k_scatter(LevelArgs a) {
       __syncthreads();
       const uint16_t* pof = a.piece_of + (size_t)g * nid;
       for (uint32_t i = tid; i < nid; i += NT) piece_of[i] = pof[i];
-      load_classifier<K>(cs, (const K*)a.spl + (size_t)g * (a.B - 1), (const ClsHead<K>*)a.cls_head + g,
-                         a.J2 + (size_t)g * kCells, a.B, a.logBp, TREE, NT);
       P = a.npieces[g];
       cur_g = g;
     }
     // run offset of every piece for this chunk: piece start + earlier chunks' keys of
     // all the piece's buckets
     const uint32_t* pst = a.piece_start + (size_t)g * nid;
-    for (uint32_t p = tid; p < P; p += NT) run_off[p] = sg.begin + pst[p];
+    for (uint32_t p = tid; p < P; p += NT) dbase[p] = sg.begin + pst[p];
     __syncthreads();
     const uint32_t* coff = a.counts + (size_t)k * nid;
     for (uint32_t i = tid; i < nid; i += NT) {
       const uint32_t c = coff[i];
-      if (c) atomicAdd(&run_off[piece_of[i]], c);
+      if (c) atomicAdd(&dbase[piece_of[i]], c);
     }
     const uint32_t lo = sg.begin + (k - si.item_off) * a.CH;
     const uint32_t hi = (uint32_t)min((uint64_t)lo + a.CH, (uint64_t)sg.end);
@@ -284,32 +294,34 @@ __global__ void __launch_bounds__(256) k_scatter(LevelArgs a) {
         for (uint32_t i = tid; i < (uint32_t)Cfg::W * hw; i += NT)
           ((uint32_t*)(cnt + (i / hw) * S))[i % hw] = 0;
       }
-      // 1. load, classify, rank among the warp's keys of the same piece
+      // 1. load keys and ids, rank among the warp's keys of the same piece
       K x[R];
+      uint16_t pc[R];
       uint64_t v[PAIRS ? R : 1];
 #pragma unroll
       for (int q = 0; q < R; ++q) {
         const uint32_t p = w * 32 * R + q * 32 + lane;
-        x[q] = p < tn ? order_in<K>(src[t0 + p], a.tf_src) : K(0);
-        if constexpr (PAIRS) v[q] = p < tn ? a.vsrc[t0 + p] : 0ull;
+        const bool ok = p < tn;
+        x[q] = ok ? order_in<K>(src[t0 + p], a.tf_src) : K(0);
+        pc[q] = ok ? ids[t0 + p] : (uint16_t)0xFFFF;
+        if constexpr (PAIRS) v[q] = ok ? a.vsrc[t0 + p] : 0ull;
       }
       __syncthreads();
       uint32_t pk[R];
       uint16_t* crow = cnt + w * S;
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        const uint32_t p = w * 32 * R + q * 32 + lane;
-        const uint32_t pc = p < tn ? piece_of[classify<K>(cs, TREE, a.logBp, a.B, x[q])] : P;
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, pc);
+        const uint32_t p = pc[q] == 0xFFFF ? P : piece_of[pc[q]];
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, p);
         const uint32_t rk = __popc(peers & ltm);
-        const uint32_t base = crow[pc];
+        const uint32_t base = crow[p];
         __syncwarp();
-        if (rk == 0) crow[pc] = (uint16_t)(base + __popc(peers));
+        if (rk == 0) crow[p] = (uint16_t)(base + __popc(peers));
         __syncwarp();
-        pk[q] = (pc << 16) | (base + rk);
+        pk[q] = (p << 16) | (base + rk);
       }
       __syncthreads();
-      // 2. piece totals, scan over pieces, per-warp starts
+      // 2. piece totals, scan over pieces, per-warp starts, destination bases
       for (uint32_t p = tid; p <= P; p += NT) {
         uint32_t s = 0;
 #pragma unroll
@@ -343,42 +355,35 @@ __global__ void __launch_bounds__(256) k_scatter(LevelArgs a) {
         }
       }
       __syncthreads();
-      // 3. stage by tile position (piece-major, input order inside a piece)
+      // 3. stage by tile position (piece-major, input order inside a piece), with the
+      //    key's destination: piece run offset + its place in the piece's tile run
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        const uint32_t pc = pk[q] >> 16;
-        const uint32_t pos = crow[pc] + (pk[q] & 0xFFFF);
+        const uint32_t p = pk[q] >> 16;
+        const uint32_t pos = crow[p] + (pk[q] & 0xFFFF);
         stage_key[pos] = x[q];
-        stage_id[pos] = (uint16_t)pc;
+        if (p < P) stage_dst[pos] = dbase[p] + (pos - tstart[p]);
         if constexpr (PAIRS) stage_val[pos] = v[q];
       }
       __syncthreads();
       // 4. one contiguous run per piece
       for (uint32_t p = tid; p < tn; p += NT) {
-        const uint32_t pc = stage_id[p];
-        const uint32_t d = run_off[pc] + (p - tstart[pc]);
+        const uint32_t d = stage_dst[p];
         dst[d] = stage_key[p];
         if constexpr (PAIRS) a.vdst[d] = stage_val[p];
       }
-      __syncthreads();
-      for (uint32_t p = tid; p < P; p += NT) run_off[p] += (uint32_t)tstart[p + 1] - tstart[p];
+      for (uint32_t p = tid; p < P; p += NT) dbase[p] += (uint32_t)tstart[p + 1] - tstart[p];
       __syncthreads();
     }
   }
 }
 
 // ------------------------------------------------------------------------ launchers
-size_t scatter_smem_bytes(int ksize, bool pairs, uint32_t B, bool tree) {
-  size_t off[9];
-#define AMS_SZ(K, P, T) return scatter_smem_layout<K, P, T>(B, off)
-  if (ksize == 4) {
-    if (pairs) { if (tree) AMS_SZ(uint32_t, true, true); else AMS_SZ(uint32_t, true, false); }
-    else { if (tree) AMS_SZ(uint32_t, false, true); else AMS_SZ(uint32_t, false, false); }
-  } else {
-    if (pairs) { if (tree) AMS_SZ(uint64_t, true, true); else AMS_SZ(uint64_t, true, false); }
-    else { if (tree) AMS_SZ(uint64_t, false, true); else AMS_SZ(uint64_t, false, false); }
-  }
-#undef AMS_SZ
+size_t scatter_smem_bytes(int ksize, bool pairs, uint32_t B) {
+  size_t off[8];
+  if (ksize == 4)
+    return pairs ? scatter_smem_layout<uint32_t, true>(B, off) : scatter_smem_layout<uint32_t, false>(B, off);
+  return pairs ? scatter_smem_layout<uint64_t, true>(B, off) : scatter_smem_layout<uint64_t, false>(B, off);
 }
 
 size_t classify_smem_bytes(int ksize, uint32_t B, bool tree) {
@@ -401,19 +406,13 @@ cudaError_t launch_table(const LevelArgs& a, int ksize, int grid, cudaStream_t s
   return cudaGetLastError();
 }
 
-cudaError_t launch_classify(const LevelArgs& a, int ksize, bool tree, int grid, uint16_t* ids_out,
-                            cudaStream_t s) {
+cudaError_t launch_classify(const LevelArgs& a, int ksize, bool tree, int grid, cudaStream_t s) {
   const size_t sm = classify_smem_bytes(ksize, a.B, tree);
   cudaError_t e;
-#define AMS_LAUNCH_CLS(K, T)                                                      \
-  do {                                                                            \
-    if (ids_out) {                                                                \
-      if ((e = set_smem(k_classify<K, T, true>, sm)) != cudaSuccess) return e;    \
-      k_classify<K, T, true><<<grid, 512, sm, s>>>(a, ids_out);                   \
-    } else {                                                                      \
-      if ((e = set_smem(k_classify<K, T, false>, sm)) != cudaSuccess) return e;   \
-      k_classify<K, T, false><<<grid, 512, sm, s>>>(a, ids_out);                  \
-    }                                                                             \
+#define AMS_LAUNCH_CLS(K, T)                                            \
+  do {                                                                  \
+    if ((e = set_smem(k_classify<K, T>, sm)) != cudaSuccess) return e;  \
+    k_classify<K, T><<<grid, 512, sm, s>>>(a);                          \
   } while (0)
   if (ksize == 4) {
     if (tree) AMS_LAUNCH_CLS(uint32_t, true); else AMS_LAUNCH_CLS(uint32_t, false);
@@ -429,20 +428,18 @@ cudaError_t launch_scan(const LevelArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_scatter(const LevelArgs& a, int ksize, bool pairs, bool tree, int grid, cudaStream_t s) {
-  const size_t sm = scatter_smem_bytes(ksize, pairs, a.B, tree);
+cudaError_t launch_scatter(const LevelArgs& a, int ksize, bool pairs, int grid, cudaStream_t s) {
+  const size_t sm = scatter_smem_bytes(ksize, pairs, a.B);
   cudaError_t e;
-#define AMS_LAUNCH_SCATTER(K, P, T)                                         \
+#define AMS_LAUNCH_SCATTER(K, P)                                            \
   do {                                                                      \
-    if ((e = set_smem(k_scatter<K, P, T>, sm)) != cudaSuccess) return e;    \
-    k_scatter<K, P, T><<<grid, 256, sm, s>>>(a);                            \
+    if ((e = set_smem(k_scatter<K, P>, sm)) != cudaSuccess) return e;       \
+    k_scatter<K, P><<<grid, 256, sm, s>>>(a);                               \
   } while (0)
   if (ksize == 4) {
-    if (pairs) { if (tree) AMS_LAUNCH_SCATTER(uint32_t, true, true); else AMS_LAUNCH_SCATTER(uint32_t, true, false); }
-    else { if (tree) AMS_LAUNCH_SCATTER(uint32_t, false, true); else AMS_LAUNCH_SCATTER(uint32_t, false, false); }
+    if (pairs) AMS_LAUNCH_SCATTER(uint32_t, true); else AMS_LAUNCH_SCATTER(uint32_t, false);
   } else {
-    if (pairs) { if (tree) AMS_LAUNCH_SCATTER(uint64_t, true, true); else AMS_LAUNCH_SCATTER(uint64_t, true, false); }
-    else { if (tree) AMS_LAUNCH_SCATTER(uint64_t, false, true); else AMS_LAUNCH_SCATTER(uint64_t, false, false); }
+    if (pairs) AMS_LAUNCH_SCATTER(uint64_t, true); else AMS_LAUNCH_SCATTER(uint64_t, false);
   }
 #undef AMS_LAUNCH_SCATTER
   return cudaGetLastError();
