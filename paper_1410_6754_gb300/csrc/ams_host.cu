@@ -142,7 +142,7 @@ size_t carve(const Plan& p, char* base, Bufs* b) {
   b->status = c.take<uint32_t>(64);
   b->ctr = c.take<LevelCounters>(kMaxLevels + 1);
   b->tmp = c.take<char>(p.n * p.ksize);
-  b->ids = c.take<uint16_t>(p.n);
+  b->ids = c.take<uint16_t>(p.n + 8);  // the scatter copies ids in 4-byte words
   b->vtmp = p.pairs ? c.take<uint64_t>(p.n) : nullptr;
   b->segs1 = c.take<Seg>(p.seg1_cap + 1);
   b->bc0 = c.take<BcItem>(p.bc0_cap);
@@ -452,7 +452,7 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
     ln.begin(AMS_K_BINPACK);
     AMS_TRY(ln.end(launch_binpack(la, seg_grid, s)));
     ln.begin(AMS_K_SCATTER);
-    AMS_TRY(ln.end(launch_scatter(la, p.ksize, p.pairs, SM * 2, s)));
+    AMS_TRY(ln.end(launch_scatter(la, p.ksize, p.pairs, /*stable=*/p.pairs, SM * 2, s)));
     if ((st = run_basecase(la.dst, la.vdst, lb.bc, &b.ctr[l].n_bc, 0, lp.bc_cap, false)) != AMS_OK)
       return st;
     if (la.last && (st = run_basecase(la.dst, la.vdst, b.big, &b.ctr[l].n_big, 0, p.big_cap, true)) != AMS_OK)
@@ -958,7 +958,7 @@ ams_status ams_step_partition(const void* d_in, void* d_out, const uint64_t* d_v
   AMS_TRY(launch_classify(la, ks, false, cx->sm_count * 4, s));
   AMS_TRY(launch_scan(la, cx->sm_count * 8, s));
   AMS_TRY(launch_binpack(la, 1, s));
-  AMS_TRY(launch_scatter(la, ks, d_vals_in != nullptr, cx->sm_count * 2, s));
+  AMS_TRY(launch_scatter(la, ks, d_vals_in != nullptr, /*stable=*/true, cx->sm_count * 2, s));
   return AMS_OK;
 }
 

@@ -212,11 +212,12 @@ cudaError_t launch_table(const LevelArgs& a, int ksize, int grid, cudaStream_t s
 cudaError_t launch_classify(const LevelArgs& a, int ksize, bool tree, int grid, cudaStream_t s);
 cudaError_t launch_scan(const LevelArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_binpack(const LevelArgs& a, int grid, cudaStream_t s);
-cudaError_t launch_scatter(const LevelArgs& a, int ksize, bool pairs, int grid, cudaStream_t s);
+cudaError_t launch_scatter(const LevelArgs& a, int ksize, bool pairs, bool stable, int grid,
+                           cudaStream_t s);
 cudaError_t launch_basecase(const BaseArgs& a, int ksize, bool pairs, bool big, int grid, cudaStream_t s);
 
 // shared-memory bytes each kernel needs (for occupancy and opt-in)
-size_t scatter_smem_bytes(int ksize, bool pairs, uint32_t B);
+size_t scatter_smem_bytes(int ksize, bool pairs, bool stable, uint32_t B);
 size_t classify_smem_bytes(int ksize, uint32_t B, bool tree);
 size_t basecase_smem_bytes(int ksize, bool pairs);
 uint32_t basecase_max_cap(int ksize, bool pairs);

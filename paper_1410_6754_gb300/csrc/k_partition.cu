@@ -5,13 +5,7 @@
 //             the scatter); per-chunk bucket counts
 //   scan      per (segment, id): exclusive prefix of the counts over the segment's
 //             chunks, and the bucket totals
-//   scatter   group-wise delivery: every key goes to its *piece* (a run of buckets of
-//             one group, or a final equality bucket; the pieces are made by the
-//             bin-packing kernel), at piece start + chunk offset + its rank among the
-//             chunk's keys of that piece in input order.  Per tile of keys the ranks
-//             come from warp-level match ranking and a scan over (piece, warp)
-//             counters; keys are staged piece-major in shared memory so that every
-//             piece receives one contiguous run per tile.
+// (the delivery itself is in k_scatter.cu)
 #include "classifier.cuh"
 #include "cta_utils.cuh"
 
@@ -199,193 +193,7 @@ __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
   }
 }
 
-// -------------------------------------------------------------------------- scatter
-// Block of 256 threads = 8 warps; warp w owns keys [w*32R, (w+1)*32R) of a tile of
-// 256R keys; lane l of round q holds key w*32R + 32q + l.  The bucket ids come from
-// the classify pass.
-template <typename K, bool PAIRS>
-struct ScatterCfg {
-  static constexpr int NT = 256;
-  static constexpr int W = NT / 32;
-  static constexpr int R = PAIRS ? 8 : 16;
-  static constexpr int TILE = NT * R;
-};
-
-template <typename K, bool PAIRS>
-__host__ __device__ constexpr size_t scatter_smem_layout(uint32_t B, size_t* off) {
-  // offsets: piece_of, cnt, tstart, dbase, stage_key, stage_dst, stage_val, ws
-  using C = ScatterCfg<K, PAIRS>;
-  const uint32_t nid = 2 * B - 1;
-  const uint32_t S = (nid + 2) & ~1u;  // counter row stride (entries)
-  size_t o = 0;
-  off[0] = o; o += (size_t)nid * 2;
-  o = (o + 15) & ~(size_t)15;
-  off[1] = o; o += (size_t)C::W * S * 2;
-  off[2] = o; o += (size_t)(nid + 2) * 2;
-  o = (o + 15) & ~(size_t)15;
-  off[3] = o; o += (size_t)nid * 4;
-  o = (o + 15) & ~(size_t)15;
-  off[4] = o; o += (size_t)C::TILE * sizeof(K);
-  off[5] = o; o += (size_t)C::TILE * 4;
-  o = (o + 15) & ~(size_t)15;
-  off[6] = o; o += PAIRS ? (size_t)C::TILE * 8 : 0;
-  off[7] = o; o += 64 * 4;
-  return o;
-}
-
-template <typename K, bool PAIRS>
-__global__ void __launch_bounds__(256) k_scatter(LevelArgs a) {
-  using Cfg = ScatterCfg<K, PAIRS>;
-  constexpr int NT = Cfg::NT, R = Cfg::R, TILE = Cfg::TILE;
-  extern __shared__ __align__(16) unsigned char smem[];
-  size_t off[8];
-  scatter_smem_layout<K, PAIRS>(a.B, off);
-  const uint32_t nid = a.nid;
-  const uint32_t S = (nid + 2) & ~1u;
-  uint16_t* piece_of = (uint16_t*)(smem + off[0]);
-  uint16_t* cnt = (uint16_t*)(smem + off[1]);
-  uint16_t* tstart = (uint16_t*)(smem + off[2]);
-  uint32_t* dbase = (uint32_t*)(smem + off[3]);  // run offset of each piece
-  K* stage_key = (K*)(smem + off[4]);
-  uint32_t* stage_dst = (uint32_t*)(smem + off[5]);
-  uint64_t* stage_val = (uint64_t*)(smem + off[6]);
-  uint32_t* ws = (uint32_t*)(smem + off[7]);
-
-  const uint32_t nseg = a.ctr->nseg;
-  const uint32_t items = a.ctr->items;
-  const K* src = (const K*)a.src;
-  const uint16_t* ids = a.ids;
-  K* dst = (K*)a.dst;
-  const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const uint32_t ltm = lanemask_lt();
-  uint32_t cur_g = 0xFFFFFFFFu;
-  uint32_t P = 0;
-
-  for (uint32_t k = blockIdx.x; k < items; k += gridDim.x) {
-    const uint32_t g = find_seg<&SegInfo::item_off>(a.sinfo, nseg, k);
-    const SegInfo si = a.sinfo[g];
-    const Seg sg = a.segs[g];
-    if (g != cur_g) {
-      __syncthreads();
-      const uint16_t* pof = a.piece_of + (size_t)g * nid;
-      for (uint32_t i = tid; i < nid; i += NT) piece_of[i] = pof[i];
-      P = a.npieces[g];
-      cur_g = g;
-    }
-    // run offset of every piece for this chunk: piece start + earlier chunks' keys of
-    // all the piece's buckets
-    const uint32_t* pst = a.piece_start + (size_t)g * nid;
-    for (uint32_t p = tid; p < P; p += NT) dbase[p] = sg.begin + pst[p];
-    __syncthreads();
-    const uint32_t* coff = a.counts + (size_t)k * nid;
-    for (uint32_t i = tid; i < nid; i += NT) {
-      const uint32_t c = coff[i];
-      if (c) atomicAdd(&dbase[piece_of[i]], c);
-    }
-    const uint32_t lo = sg.begin + (k - si.item_off) * a.CH;
-    const uint32_t hi = (uint32_t)min((uint64_t)lo + a.CH, (uint64_t)sg.end);
-    __syncthreads();
-
-    for (uint32_t t0 = lo; t0 < hi; t0 += TILE) {
-      const uint32_t tn = min((uint32_t)TILE, hi - t0);
-      {
-        // counters of pieces 0..P (P = the dummy piece of the tile's empty slots)
-        const uint32_t hw = (P + 2) / 2;  // 32-bit words per warp row
-        for (uint32_t i = tid; i < (uint32_t)Cfg::W * hw; i += NT)
-          ((uint32_t*)(cnt + (i / hw) * S))[i % hw] = 0;
-      }
-      // 1. load keys and ids, rank among the warp's keys of the same piece
-      K x[R];
-      uint16_t pc[R];
-      uint64_t v[PAIRS ? R : 1];
-#pragma unroll
-      for (int q = 0; q < R; ++q) {
-        const uint32_t p = w * 32 * R + q * 32 + lane;
-        const bool ok = p < tn;
-        x[q] = ok ? order_in<K>(src[t0 + p], a.tf_src) : K(0);
-        pc[q] = ok ? ids[t0 + p] : (uint16_t)0xFFFF;
-        if constexpr (PAIRS) v[q] = ok ? a.vsrc[t0 + p] : 0ull;
-      }
-      __syncthreads();
-      uint32_t pk[R];
-      uint16_t* crow = cnt + w * S;
-#pragma unroll
-      for (int q = 0; q < R; ++q) {
-        const uint32_t p = pc[q] == 0xFFFF ? P : piece_of[pc[q]];
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, p);
-        const uint32_t rk = __popc(peers & ltm);
-        const uint32_t base = crow[p];
-        __syncwarp();
-        if (rk == 0) crow[p] = (uint16_t)(base + __popc(peers));
-        __syncwarp();
-        pk[q] = (p << 16) | (base + rk);
-      }
-      __syncthreads();
-      // 2. piece totals, scan over pieces, per-warp starts, destination bases
-      for (uint32_t p = tid; p <= P; p += NT) {
-        uint32_t s = 0;
-#pragma unroll
-        for (int j = 0; j < Cfg::W; ++j) s += cnt[j * S + p];
-        tstart[p] = (uint16_t)s;
-      }
-      __syncthreads();
-      {
-        const uint32_t m = P + 1;
-        const uint32_t chunk = (m + NT - 1) / NT;
-        const uint32_t b = tid * chunk, e = min(b + chunk, m);
-        uint32_t s = 0;
-        for (uint32_t i = b; i < e; ++i) s += tstart[i];
-        uint32_t total;
-        uint32_t r = block_exclusive_scan<NT, uint32_t>(s, ws, total);
-        for (uint32_t i = b; i < e; ++i) {
-          const uint32_t t = tstart[i];
-          tstart[i] = (uint16_t)r;
-          r += t;
-        }
-        if (tid == 0) tstart[m] = (uint16_t)total;
-      }
-      __syncthreads();
-      for (uint32_t p = tid; p <= P; p += NT) {
-        uint32_t base = tstart[p];
-#pragma unroll
-        for (int j = 0; j < Cfg::W; ++j) {
-          const uint32_t t = cnt[j * S + p];
-          cnt[j * S + p] = (uint16_t)base;
-          base += t;
-        }
-      }
-      __syncthreads();
-      // 3. stage by tile position (piece-major, input order inside a piece), with the
-      //    key's destination: piece run offset + its place in the piece's tile run
-#pragma unroll
-      for (int q = 0; q < R; ++q) {
-        const uint32_t p = pk[q] >> 16;
-        const uint32_t pos = crow[p] + (pk[q] & 0xFFFF);
-        stage_key[pos] = x[q];
-        if (p < P) stage_dst[pos] = dbase[p] + (pos - tstart[p]);
-        if constexpr (PAIRS) stage_val[pos] = v[q];
-      }
-      __syncthreads();
-      // 4. one contiguous run per piece
-      for (uint32_t p = tid; p < tn; p += NT) {
-        const uint32_t d = stage_dst[p];
-        dst[d] = stage_key[p];
-        if constexpr (PAIRS) a.vdst[d] = stage_val[p];
-      }
-      for (uint32_t p = tid; p < P; p += NT) dbase[p] += (uint32_t)tstart[p + 1] - tstart[p];
-      __syncthreads();
-    }
-  }
-}
-
 // ------------------------------------------------------------------------ launchers
-size_t scatter_smem_bytes(int ksize, bool pairs, uint32_t B) {
-  size_t off[8];
-  if (ksize == 4)
-    return pairs ? scatter_smem_layout<uint32_t, true>(B, off) : scatter_smem_layout<uint32_t, false>(B, off);
-  return pairs ? scatter_smem_layout<uint64_t, true>(B, off) : scatter_smem_layout<uint64_t, false>(B, off);
-}
-
 size_t classify_smem_bytes(int ksize, uint32_t B, bool tree) {
   uint32_t Bp = 1;
   while (Bp < B) Bp <<= 1;
@@ -425,23 +233,6 @@ cudaError_t launch_classify(const LevelArgs& a, int ksize, bool tree, int grid, 
 
 cudaError_t launch_scan(const LevelArgs& a, int grid, cudaStream_t s) {
   k_scan<<<grid, 256, 0, s>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_scatter(const LevelArgs& a, int ksize, bool pairs, int grid, cudaStream_t s) {
-  const size_t sm = scatter_smem_bytes(ksize, pairs, a.B);
-  cudaError_t e;
-#define AMS_LAUNCH_SCATTER(K, P)                                            \
-  do {                                                                      \
-    if ((e = set_smem(k_scatter<K, P>, sm)) != cudaSuccess) return e;       \
-    k_scatter<K, P><<<grid, 256, sm, s>>>(a);                               \
-  } while (0)
-  if (ksize == 4) {
-    if (pairs) AMS_LAUNCH_SCATTER(uint32_t, true); else AMS_LAUNCH_SCATTER(uint32_t, false);
-  } else {
-    if (pairs) AMS_LAUNCH_SCATTER(uint64_t, true); else AMS_LAUNCH_SCATTER(uint64_t, false);
-  }
-#undef AMS_LAUNCH_SCATTER
   return cudaGetLastError();
 }
 
