@@ -3,7 +3,7 @@
 (r1 = r2 = 256 groups, overpartitioning b = 4), keys/s, per GPU or summed over ranks.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ams|reference]
-                    [--workload two_level_u64|single_level_u32]
+                    [--workload two_level_u64|two_level_u64_2e26|single_level_u32]
 
 One step sorts the whole input once (out of place, so every step sees the same
 unsorted input; the 2 GiB input and output exceed the L2 cache, so no flush is
@@ -32,6 +32,11 @@ WORKLOADS = {
     "two_level_u64": dict(n=1 << 28, bits=64, kt=1, levels=2, buckets=[256, 256], b=4, a=0,
                           dist="uniform", dtype="u64",
                           desc="2-level AMS-sort, 2^28 uniform uint64 keys, r=256x256, b=4"),
+    # the profiling case: same kernels and leaf sizes (about 4096 keys) at a quarter of
+    # the keys, 512 MiB in and out (above L2, small enough for ncu's replay passes)
+    "two_level_u64_2e26": dict(n=1 << 26, bits=64, kt=1, levels=2, buckets=[256, 64], b=4, a=0,
+                               dist="uniform", dtype="u64",
+                               desc="2-level AMS-sort, 2^26 uniform uint64 keys, r=256x64, b=4"),
     "single_level_u32": dict(n=1 << 20, bits=32, kt=0, levels=1, buckets=[256], b=1, a=16,
                              dist="uniform", dtype="u32",
                              desc="1-level sample sort, 2^20 uniform uint32 keys, 256 buckets, a=16"),
@@ -291,7 +296,8 @@ def run_ams(args, wl):
             "config": {"workload": wl["desc"], "n": n, "levels": wl["levels"],
                        "buckets": wl["buckets"], "b": wl["b"], "a": wl["a"] or "ceil(1.6 log10 n)",
                        "parallelism": f"replicas x{world}",
-                       "l2": "input 2^28 keys and output exceed L2; no flush"},
+                       "l2": ("input and output exceed L2; no flush" if n * w > (256 << 20)
+                              else "input fits L2; no flush (not a bench line)")},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": _traffic(dom),
                          "peak_source": f"{peak_src} hbm copy bandwidth",

@@ -18,62 +18,285 @@ struct BaseCfg {
   static constexpr int NT = 512;
   static constexpr uint32_t CAP = (sizeof(K) == 4 && !PAIRS) ? 16384u : 8192u;
   static constexpr int KPT = CAP / NT;
-  // two blocks per SM when their shared memory fits (keys-only 64-bit keys)
-  static constexpr int MINB = (sizeof(K) == 8 && !PAIRS) ? 2 : 1;
+  static constexpr uint32_t CELLS = 16384;  // 16-bit counters, two per word
+  // two blocks per SM when their shared memory fits (keys only)
+  static constexpr int MINB = PAIRS ? 1 : 2;
+};
+
+template <typename K>
+struct BaseSmem {
+  K* keys;         // keys by cell slot
+  uint32_t* cw;    // cell counters, 16 bits each
+  uint16_t* pos;   // input index of each slot (pairs: the stable tiebreak)
+  uint64_t* vals;  // payloads by input index
+  K* red;          // 3 * (NT/32) keys: min / max, scan totals
 };
 
 template <typename K, bool PAIRS>
 __host__ __device__ constexpr size_t base_smem_layout(size_t* off) {
   using C = BaseCfg<K, PAIRS>;
   size_t o = 0;
-  off[0] = o; o += (size_t)C::CAP * sizeof(K);         // keys
-  off[1] = o; o += (size_t)C::CAP * 2;                 // pos
-  off[2] = o;                                          // (unused)
-  off[3] = o; o += (size_t)(C::CAP / 2 + 1) * 4;       // cells
+  off[0] = o; o += (size_t)C::CAP * sizeof(K);                          // keys
+  off[1] = o; o += (size_t)C::CELLS * 2;                                // cells
+  off[2] = o; o += PAIRS ? (size_t)C::CAP * 2 : 0;                      // pos
   o = (o + 15) & ~(size_t)15;
-  off[4] = o; o += PAIRS ? (size_t)C::CAP * 8 : 0;     // payloads
-  off[5] = o; o += (size_t)2 * (C::NT / 32) * sizeof(uint64_t);  // red
-  off[6] = o; o += (size_t)(C::NT / 32 + 1) * 4;       // ws
+  off[3] = o; o += PAIRS ? (size_t)C::CAP * 8 : 0;                      // payloads
+  off[4] = o; o += (size_t)3 * (C::NT / 32) * sizeof(uint64_t);         // red / scan
   return o;
 }
 
 template <typename K, bool PAIRS>
-__device__ __forceinline__ CellSortSmem<K> base_smem(unsigned char* smem, uint64_t** vals_s) {
-  size_t off[7];
+__device__ __forceinline__ BaseSmem<K> base_smem(unsigned char* smem) {
+  size_t off[5];
   base_smem_layout<K, PAIRS>(off);
-  *vals_s = (uint64_t*)(smem + off[4]);
-  return CellSortSmem<K>{(K*)(smem + off[0]), (uint16_t*)(smem + off[1]), (uint32_t*)(smem + off[3]),
-                         (K*)(smem + off[5]), (uint32_t*)(smem + off[6])};
+  return BaseSmem<K>{(K*)(smem + off[0]), (uint32_t*)(smem + off[1]), (uint16_t*)(smem + off[2]),
+                     (uint64_t*)(smem + off[3]), (K*)(smem + off[4])};
 }
+
+// 16-bit cell counter c (two per 32-bit word; every count, prefix and end is <= CAP)
+__device__ __forceinline__ uint32_t cell_add(uint32_t* cw, uint32_t c) {
+  const uint32_t sh = (c & 1) << 4;
+  return (atomicAdd(&cw[c >> 1], 1u << sh) >> sh) & 0xFFFFu;
+}
+
+// Cell of key v: d = the top 32 significant bits of v - kmin (a shift by `sh`, done
+// with 32-bit shifts), then c = floor(d * scale / 2^32) -- monotone in v, and below
+// the cell count for every key up to kmax.
+template <typename K>
+struct CellMap {
+  K kmin;
+  uint32_t sh;     // (< 32 for 32-bit keys)
+  uint32_t scale;
+  __device__ __forceinline__ uint32_t operator()(K v) const {
+    const K d = (K)(v - kmin);
+    uint32_t d32;
+    if constexpr (sizeof(K) == 4) {
+      d32 = (uint32_t)d >> sh;
+    } else {
+      const uint32_t lo = (uint32_t)d, hi = (uint32_t)(d >> 32);
+      d32 = sh >= 32 ? hi >> (sh - 32) : __funnelshift_r(lo, hi, sh);
+    }
+    return __umulhi(d32, scale);
+  }
+};
 
 // Sort keys [b, b+m) of `src` (m <= CAP) and write them to `dst` at the same
 // offsets.  tf_in / tf_out: float order map on load / its inverse on store.
+//
+// Keys spread over about 2m equal-width cells of [lo, hi] (lo <= every key <= hi);
+// shared-memory atomics count the cells, a block scan gives their starts, a second
+// atomic pass gives every key a slot in its cell.  Every slot then ranks its key
+// among the keys of its cell (the all-pairs ranking of Section 4.2 on the small
+// cells) and writes it to its final place; slots are visited in a block-strided
+// order, so a warp writes near-consecutive places.  Ties: keys only by slot (equal
+// keys are indistinguishable), pairs by input index (stable).
+//
+// [lo, hi] for 64-bit keys comes from the high 32-bit words alone (lo = min << 32,
+// hi = max << 32 | 2^32-1) when those span at least 2^12 values -- the range is then
+// overstated by less than 0.1% -- and from the full keys otherwise.
 template <typename K, bool PAIRS>
 __device__ __forceinline__ void sort_block(const K* src, K* dst, const uint64_t* vsrc, uint64_t* vdst,
                                            uint32_t b, uint32_t m, int tf_in, int tf_out,
-                                           const CellSortSmem<K>& sm, uint64_t* vals_s) {
+                                           const BaseSmem<K>& sm) {
   using C = BaseCfg<K, PAIRS>;
-  K x[C::KPT];
+  constexpr int NT = C::NT, KPT = C::KPT, NW = NT / 32;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  K x[KPT];
 #pragma unroll
-  for (int q = 0; q < C::KPT; ++q) {
-    x[q] = K(0);
-    if ((uint32_t)q * C::NT >= m) break;  // the rest of the block's slots are empty
-    const uint32_t e = threadIdx.x + q * C::NT;
-    if (e < m) {
-      x[q] = order_in<K>(src[b + e], tf_in);
-      if constexpr (PAIRS) vals_s[e] = vsrc[b + e];
+  for (int q = 0; q < KPT; ++q) {
+    if ((uint32_t)q * NT >= m) break;  // (uniform) the rest of the slots are empty
+    const uint32_t e = tid + q * NT;
+    x[q] = e < m ? order_in<K>(src[b + e], tf_in) : K(0);
+    if constexpr (PAIRS) {
+      if (e < m) sm.vals[e] = vsrc[b + e];
     }
   }
-  __syncthreads();  // every load done before any store (src may equal dst)
-  cell_sort<K, C::NT, C::KPT>(x, m, C::CAP, sm, [&](uint32_t f, K v, uint32_t p) {
-    dst[b + f] = order_out<K>(v, tf_out);
-    if constexpr (PAIRS) vdst[b + f] = vals_s[p];
-  });
+  // min / max of the keys (32-bit keys) or of their high words (64-bit keys)
+  uint32_t* red32 = (uint32_t*)sm.red;  // [0, NW): minima, [NW, 2NW): maxima
+  {
+    uint32_t lo = 0xFFFFFFFFu, hi = 0;
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      if ((uint32_t)q * NT >= m) break;
+      if (tid + q * NT < m) {
+        const uint32_t h = sizeof(K) == 8 ? (uint32_t)((uint64_t)x[q] >> 32) : (uint32_t)x[q];
+        lo = min(lo, h);
+        hi = max(hi, h);
+      }
+    }
+    lo = __reduce_min_sync(0xFFFFFFFFu, lo);
+    hi = __reduce_max_sync(0xFFFFFFFFu, hi);
+    if (lane == 0) {
+      red32[w] = lo;
+      red32[NW + w] = hi;
+    }
+  }
+  __syncthreads();  // also: every load is done before any store (src may equal dst)
+  uint32_t hmin = red32[0], hmax = red32[NW];
+#pragma unroll
+  for (int i = 1; i < NW; ++i) {
+    hmin = min(hmin, red32[i]);
+    hmax = max(hmax, red32[NW + i]);
+  }
+  K kmin, kmax;
+  if constexpr (sizeof(K) == 4) {
+    kmin = (K)hmin;
+    kmax = (K)hmax;
+  } else if (hmax - hmin >= (1u << 12)) {
+    kmin = (K)hmin << 32;
+    kmax = ((K)hmax << 32) | 0xFFFFFFFFull;
+  } else {
+    // exact 64-bit bounds (keys close together)
+    K lo = key_max<K>(), hi = K(0);
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      if ((uint32_t)q * NT >= m) break;
+      if (tid + q * NT < m) {
+        lo = x[q] < lo ? x[q] : lo;
+        hi = x[q] > hi ? x[q] : hi;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const K u = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+      const K v = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+      lo = u < lo ? u : lo;
+      hi = v > hi ? v : hi;
+    }
+    __syncthreads();  // red32 read by every thread
+    if (lane == 0) {
+      sm.red[w] = lo;
+      sm.red[NW + w] = hi;
+    }
+    __syncthreads();
+    kmin = sm.red[0];
+    kmax = sm.red[NW];
+#pragma unroll
+    for (int i = 1; i < NW; ++i) {
+      kmin = sm.red[i] < kmin ? sm.red[i] : kmin;
+      kmax = sm.red[NW + i] > kmax ? sm.red[NW + i] : kmax;
+    }
+  }
+  if (kmin == kmax) {  // all keys equal: input order
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+      if ((uint32_t)q * NT >= m) break;
+      const uint32_t e = tid + q * NT;
+      if (e < m) {
+        dst[b + e] = order_out<K>(x[q], tf_out);
+        if constexpr (PAIRS) vdst[b + e] = sm.vals[e];
+      }
+    }
+    return;
+  }
+  // cells: M = 2m rounded up to 8 (whole 128-bit words of counters), at most CELLS
+  const uint32_t M = min(C::CELLS, max(8u, (2 * m + 7) & ~7u));
+  const K range = (K)(kmax - kmin);
+  const int nb = bitlen<K>(range);
+  const uint32_t sh = nb > 32 ? (uint32_t)(nb - 32) : 0u;
+  const uint32_t r32 = (uint32_t)(range >> sh);  // d of kmax
+  // scale ~ M * 2^32 / (r32 + 1), rounded down with a 2^-20 margin for the fp32
+  // rounding, so that d * scale / 2^32 < M for every d <= r32
+  const float fs = __fdividef((float)M * 4294967296.0f, (float)r32 + 1.0f) * (1.0f - 1.0f / 1048576.0f);
+  const uint32_t scale = (uint32_t)fminf(fs, 4294967040.0f);
+  const CellMap<K> cell{kmin, sh, scale};
+  const uint32_t nv = M / 8;  // 128-bit words of counters
+  for (uint32_t i = tid; i < nv; i += NT) ((uint4*)sm.cw)[i] = make_uint4(0, 0, 0, 0);
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < KPT; ++q) {
+    if ((uint32_t)q * NT >= m) break;
+    if (tid + q * NT < m) {
+      const uint32_t c = cell(x[q]);
+      atomicAdd(&sm.cw[c >> 1], 1u << ((c & 1) << 4));
+    }
+  }
+  __syncthreads();
+  // exclusive scan of the M 16-bit counters.  Warp w owns the 128-bit words
+  // [w*pv, (w+1)*pv); lane l reads word 32i + l of them (consecutive lanes,
+  // consecutive banks).  (v * 0x10001) >> 16 adds the two counters of a 32-bit word
+  // (their sum is <= CAP: no carry).
+  uint16_t* c16 = (uint16_t*)sm.cw;
+  {
+    uint32_t* ws = red32 + 2 * NW;  // (bounds above already read by every thread)
+    auto sum4 = [](const uint4& v) {
+      return ((v.x * 0x10001u) >> 16) + ((v.y * 0x10001u) >> 16) + ((v.z * 0x10001u) >> 16) +
+             ((v.w * 0x10001u) >> 16);
+    };
+    const uint32_t pv = (nv + NW - 1) / NW;
+    const uint32_t vb = min(w * pv, nv), ve = min(vb + pv, nv);
+    uint4* cv = (uint4*)sm.cw;
+    uint32_t s = 0;
+    for (uint32_t i = vb + lane; i < ve; i += 32) s += sum4(cv[i]);
+    s = __reduce_add_sync(0xFFFFFFFFu, s);
+    if (lane == 0) ws[w] = s;
+    __syncthreads();
+    uint32_t carry = 0;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) carry += i < (int)w ? ws[i] : 0u;
+    for (uint32_t i0 = vb; i0 < ve; i0 += 32) {  // (warp-uniform trip count)
+      const uint32_t i = i0 + lane;
+      uint4 v = i < ve ? cv[i] : make_uint4(0, 0, 0, 0);
+      const uint32_t t = sum4(v);
+      uint32_t inc = t;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= (uint32_t)o) inc += y;
+      }
+      uint32_t run = carry + inc - t;
+      auto pre = [&](uint32_t u) {  // word (lo, hi) -> (run, run + lo)
+        const uint32_t o = run * 0x10001u + (u << 16);
+        run += (u * 0x10001u) >> 16;
+        return o;
+      };
+      v.x = pre(v.x);
+      v.y = pre(v.y);
+      v.z = pre(v.z);
+      v.w = pre(v.w);
+      if (i < ve) cv[i] = v;
+      carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < KPT; ++q) {
+    if ((uint32_t)q * NT >= m) break;
+    const uint32_t e = tid + q * NT;
+    if (e < m) {
+      const uint32_t s = cell_add(sm.cw, cell(x[q]));  // afterwards: the cell's end
+      sm.keys[s] = x[q];
+      if constexpr (PAIRS) sm.pos[s] = (uint16_t)e;
+    }
+  }
+  __syncthreads();
+  for (uint32_t s = tid; s < m; s += NT) {
+    const K v = sm.keys[s];
+    const uint32_t c = cell(v);
+    const uint32_t cb = c ? c16[c - 1] : 0u, ce = c16[c];
+    uint32_t r = 0;
+    if constexpr (PAIRS) {
+      const uint32_t p = sm.pos[s];
+#pragma unroll 1
+      for (uint32_t t = cb; t < ce; ++t) {
+        const K y = sm.keys[t];
+        r += (y < v) | ((y == v) & (sm.pos[t] < p));
+      }
+      dst[b + cb + r] = order_out<K>(v, tf_out);
+      vdst[b + cb + r] = sm.vals[p];
+    } else {
+      // (key, slot) order: slots before s count when <= v, slots after when < v
+#pragma unroll 1
+      for (uint32_t t = cb; t < s; ++t) r += sm.keys[t] <= v;
+#pragma unroll 1
+      for (uint32_t t = s + 1; t < ce; ++t) r += sm.keys[t] < v;
+      dst[b + cb + r] = order_out<K>(v, tf_out);
+    }
+  }
 }
 
 template <typename K, bool PAIRS>
-__device__ void big_sort(const BaseArgs& a, uint32_t b, uint32_t m, const CellSortSmem<K>& sm,
-                         uint64_t* vals_s) {
+__device__ void big_sort(const BaseArgs& a, uint32_t b, uint32_t m, const BaseSmem<K>& sm) {
   using C = BaseCfg<K, PAIRS>;
   const K* src = (const K*)a.src;
   K* out = (K*)a.out;
@@ -88,8 +311,7 @@ __device__ void big_sort(const BaseArgs& a, uint32_t b, uint32_t m, const CellSo
   for (uint32_t r = 0; r < runs; ++r) {
     const uint32_t rb = b + r * C::CAP;
     const uint32_t rm = min(C::CAP, m - r * C::CAP);
-    sort_block<K, PAIRS>(src, bufA, a.vsrc, vA, rb, rm, a.tf_load, passes == 0 ? a.tf_store : 0, sm,
-                         vals_s);
+    sort_block<K, PAIRS>(src, bufA, a.vsrc, vA, rb, rm, a.tf_load, passes == 0 ? a.tf_store : 0, sm);
     __syncthreads();
   }
   K* cur = bufA;
@@ -127,8 +349,7 @@ template <typename K, bool PAIRS>
 __global__ void __launch_bounds__(512, BaseCfg<K, PAIRS>::MINB) k_basecase(BaseArgs a) {
   using C = BaseCfg<K, PAIRS>;
   extern __shared__ __align__(16) unsigned char smem[];
-  uint64_t* vals_s;
-  const CellSortSmem<K> sm = base_smem<K, PAIRS>(smem, &vals_s);
+  const BaseSmem<K> sm = base_smem<K, PAIRS>(smem);
   const uint32_t nitems = *a.nitems;
   const K* src = (const K*)a.src;
   K* out = (K*)a.out;
@@ -141,7 +362,7 @@ __global__ void __launch_bounds__(512, BaseCfg<K, PAIRS>::MINB) k_basecase(BaseA
         if constexpr (PAIRS) a.vout[b + e] = a.vsrc[b + e];
       }
     } else if (m <= C::CAP) {
-      sort_block<K, PAIRS>(src, out, a.vsrc, a.vout, b, m, a.tf_load, a.tf_store, sm, vals_s);
+      sort_block<K, PAIRS>(src, out, a.vsrc, a.vout, b, m, a.tf_load, a.tf_store, sm);
     }
     __syncthreads();
   }
@@ -152,18 +373,17 @@ __global__ void __launch_bounds__(512, BaseCfg<K, PAIRS>::MINB) k_basecase(BaseA
 template <typename K, bool PAIRS>
 __global__ void __launch_bounds__(512) k_bigsort(BaseArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  uint64_t* vals_s;
-  const CellSortSmem<K> sm = base_smem<K, PAIRS>(smem, &vals_s);
+  const BaseSmem<K> sm = base_smem<K, PAIRS>(smem);
   const uint32_t nitems = *a.nitems;
   for (uint32_t it = blockIdx.x; it < nitems; it += gridDim.x) {
     const BcItem item = a.items[it];
-    big_sort<K, PAIRS>(a, item.begin, item.end - item.begin, sm, vals_s);
+    big_sort<K, PAIRS>(a, item.begin, item.end - item.begin, sm);
     __syncthreads();
   }
 }
 
 size_t basecase_smem_bytes(int ksize, bool pairs) {
-  size_t off[7];
+  size_t off[5];
   if (ksize == 4) return pairs ? base_smem_layout<uint32_t, true>(off) : base_smem_layout<uint32_t, false>(off);
   return pairs ? base_smem_layout<uint64_t, true>(off) : base_smem_layout<uint64_t, false>(off);
 }
@@ -224,10 +444,9 @@ __global__ void __launch_bounds__(512) k_sort_noalloc(void* keys, uint64_t* vals
                                                       uint64_t* scratch) {
   using C = BaseCfg<K, PAIRS>;
   extern __shared__ __align__(16) unsigned char smem[];
-  uint64_t* vals_s;
-  const CellSortSmem<K> sm = base_smem<K, PAIRS>(smem, &vals_s);
+  const BaseSmem<K> sm = base_smem<K, PAIRS>(smem);
   if (n <= C::CAP) {
-    sort_block<K, PAIRS>((const K*)keys, (K*)keys, vals, vals, 0, n, tf, tf, sm, vals_s);
+    sort_block<K, PAIRS>((const K*)keys, (K*)keys, vals, vals, 0, n, tf, tf, sm);
     return;
   }
   BaseArgs a{};
@@ -239,7 +458,7 @@ __global__ void __launch_bounds__(512) k_sort_noalloc(void* keys, uint64_t* vals
   a.vscratch = scratch + kNoallocMax;  // payload part
   a.tf_load = tf;
   a.tf_store = tf;
-  big_sort<K, PAIRS>(a, 0, n, sm, vals_s);
+  big_sort<K, PAIRS>(a, 0, n, sm);
 }
 
 }  // namespace ams
