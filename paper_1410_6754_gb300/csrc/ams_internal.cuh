@@ -26,7 +26,7 @@ constexpr int kMaxLevels = 8;
 constexpr int kSampleTile = 2048;       // keys per locally sorted sample tile
 constexpr uint32_t kCopyChunk = 65536;  // elements per copy work item
 constexpr int kMaxBuckets = 2048;       // largest b*r per level
-constexpr uint32_t kCellTable = 4096;   // cells of the table classifier
+constexpr uint32_t kCellTable = 16384;  // cells of the table classifier
 constexpr int kThrCount = 48;           // oversampling thresholds 10^(a/1.6)
 
 // base-case work item kinds

@@ -6,10 +6,12 @@
 //  * tree:  the implicit search tree of the paper's multisplitter, i <- 2i + [t_i < x]
 //           for log2(B') levels (B' = B rounded up to a power of two);
 //  * table: a radix-assisted start.  The splitter range [s_0, s_{B-2}] is cut into
-//           4096 equal-width cells; J[c] = #{splitters below cell c}.  A key's cell
-//           bounds j to [J[c], J[c+1]], and a branch-free binary search over that
-//           short span (a fixed number of steps per segment: the widest span of the
-//           segment) finishes it.  Cost: one table load plus a few compares instead of
+//           16384 equal-width cells by a monotone cell function; J[c] = #{splitters
+//           whose cell is below c}.  A key's cell bounds j to [J[c], J[c+1]] (every
+//           splitter of a lower cell is smaller than the key, every splitter of a
+//           higher cell larger), and a branch-free binary search over that short span
+//           (a fixed number of steps per segment: the widest span of the segment)
+//           finishes it.  Cost: one table load plus a few compares instead of
 //           log2(B') dependent loads.
 #pragma once
 
@@ -17,7 +19,7 @@
 
 namespace ams {
 
-constexpr int kCellBits = 12;
+constexpr int kCellBits = 14;
 constexpr uint32_t kCells = 1u << kCellBits;
 static_assert(kCells == kCellTable, "cell table size");
 
@@ -25,24 +27,41 @@ static_assert(kCells == kCellTable, "cell table size");
 template <typename K>
 struct ClsHead {
   K lo;            // smallest splitter
-  uint32_t sh;     // cell = (x - lo) >> sh
+  uint32_t sh;     // cell width 2^sh
   uint32_t steps;  // binary-search steps that resolve the widest span
 };
+
+// Cell of key x: min(kCells-1, max(x - lo, 0) >> sh), computed for 64-bit keys
+// from the high 32-bit words alone once sh >= 32 (then the cell of x is
+// (max(hi(x), hi(lo)) - hi(lo)) >> (sh - 32), clamped: still monotone in x, and the
+// table is built with this same function).
+template <typename K>
+__device__ __forceinline__ uint32_t cell_of(K x, K lo, uint32_t sh) {
+  if constexpr (sizeof(K) == 8) {
+    if (sh >= 32) {
+      const uint32_t xh = (uint32_t)(x >> 32), lh = (uint32_t)(lo >> 32);
+      return min((max(xh, lh) - lh) >> (sh - 32), kCells - 1);
+    }
+    const K d = x > lo ? (K)(x - lo) : K(0);
+    const K q = d >> sh;
+    return q >= (K)kCells ? kCells - 1 : (uint32_t)q;
+  } else {
+    return min((max((uint32_t)x, (uint32_t)lo) - (uint32_t)lo) >> sh, kCells - 1);
+  }
+}
+
+// Cell width exponent of a segment whose splitters span [lo, hi].
+template <typename K>
+__device__ __forceinline__ uint32_t cell_shift(K lo, K hi) {
+  const int nb = bitlen<K>((K)(hi - lo));
+  return nb > kCellBits ? (uint32_t)(nb - kCellBits) : 0u;
+}
 
 // J2[c] = J[c] | J[c+1] << 16, c < kCells.
 template <typename K>
 __device__ __forceinline__ uint32_t table_classify(const uint32_t* J2, const K* spl, K lo, uint32_t sh,
                                                    uint32_t steps, uint32_t B, K x) {
-  constexpr int kBits = 8 * sizeof(K);
-  const K d = x - lo;
-  uint32_t c;
-  if (x < lo) {
-    c = 0;
-  } else {
-    const K q = sh >= (uint32_t)kBits ? K(0) : (d >> sh);
-    c = q >= (K)kCells ? kCells - 1 : (uint32_t)q;
-  }
-  const uint32_t jj = J2[c];
+  const uint32_t jj = J2[cell_of<K>(x, lo, sh)];
   uint32_t base = jj & 0xFFFFu;
   uint32_t len = (jj >> 16) - base;
   for (uint32_t s = 0; s < steps; ++s) {

@@ -12,44 +12,36 @@
 namespace ams {
 
 // ---------------------------------------------------------------------------- table
+// J[c] = #{splitters whose cell is below c} = the first splitter index whose cell is
+// >= c (the cells of the sorted splitters do not decrease).
 template <typename K>
 __global__ void __launch_bounds__(512) k_table(LevelArgs a) {
   constexpr int NT = 512;
-  __shared__ K spl_s[kMaxBuckets];
-  __shared__ uint16_t J_s[kCells + 1];
+  __shared__ uint32_t cs[kMaxBuckets];  // cell of every splitter
   __shared__ uint32_t ws[NT / 32 + 1];
   const uint32_t nseg = a.ctr->nseg;
-  const uint32_t B = a.B;
+  const uint32_t B = a.B, ns = B - 1;
   for (uint32_t g = blockIdx.x; g < nseg; g += gridDim.x) {
-    const K* spl_g = (const K*)a.spl + (size_t)g * (B - 1);
-    for (uint32_t i = threadIdx.x; i < B - 1; i += NT) spl_s[i] = spl_g[i];
+    const K* spl_g = (const K*)a.spl + (size_t)g * ns;
+    const K lo = spl_g[0], hi = spl_g[ns - 1];
+    const uint32_t sh = cell_shift<K>(lo, hi);
+    for (uint32_t i = threadIdx.x; i < ns; i += NT) cs[i] = cell_of<K>(spl_g[i], lo, sh);
     __syncthreads();
-    const K lo = spl_s[0], hi = spl_s[B - 2];
-    const int nb = bitlen<K>((K)(hi - lo));
-    const uint32_t sh = nb > kCellBits ? (uint32_t)(nb - kCellBits) : 0u;
-    for (uint32_t c = threadIdx.x; c <= kCells; c += NT) {
-      uint32_t j;
-      if (c == 0) {
-        j = 0;
-      } else if (c == kCells || ((K)c << sh) > (K)(key_max<K>() - lo)) {
-        j = B - 1;
-      } else {
-        const K edge = lo + ((K)c << sh);  // first key of cell c
-        uint32_t l = 0, h = B - 1;           // #{splitters < edge}
-        while (l < h) {
-          const uint32_t m = (l + h) >> 1;
-          if (spl_s[m] < edge) l = m + 1; else h = m;
-        }
-        j = l;
+    auto first_at_least = [&](uint32_t c) {  // #{i : cs[i] < c}
+      uint32_t l = 0, h = ns;
+      while (l < h) {
+        const uint32_t m = (l + h) >> 1;
+        if (cs[m] < c) l = m + 1; else h = m;
       }
-      J_s[c] = (uint16_t)j;
-    }
-    __syncthreads();
+      return l;
+    };
     uint32_t* J2 = a.J2 + (size_t)g * kCells;
     uint32_t span = 0;
     for (uint32_t c = threadIdx.x; c < kCells; c += NT) {
-      J2[c] = (uint32_t)J_s[c] | ((uint32_t)J_s[c + 1] << 16);
-      span = max(span, (uint32_t)J_s[c + 1] - J_s[c]);
+      const uint32_t j0 = first_at_least(c);
+      const uint32_t j1 = c + 1 == kCells ? ns : first_at_least(c + 1);
+      J2[c] = j0 | (j1 << 16);
+      span = max(span, j1 - j0);
     }
     const uint32_t mspan = block_reduce_max<NT, uint32_t>(span, ws);
     if (threadIdx.x == 0) {

@@ -4,7 +4,7 @@
 // kernel) at: piece start + the keys of that piece in earlier chunks (from the
 // per-chunk bucket counts) + its place among this chunk's keys of the piece.
 //
-// Keys are handled in tiles of 256R; per tile every key gets its tile position
+// Keys are handled in tiles of 256R keys; per tile every key gets its tile position
 // (piece-major), keys are staged by tile position in shared memory with their
 // destinations, and every piece then receives one contiguous run.  The place of a key
 // among the tile's keys of its piece comes from one of two rankings:
@@ -20,25 +20,24 @@
 
 namespace ams {
 
-template <typename K, bool PAIRS, bool STABLE>
+template <typename K, bool PAIRS>
 struct ScatterCfg {
   static constexpr int NT = 256;
   static constexpr int W = NT / 32;
   static constexpr int R = PAIRS ? 8 : 16;
   static constexpr int TILE = NT * R;
-  static constexpr int ROWS = STABLE ? W : 1;  // counter rows
 };
 
-template <typename K, bool PAIRS, bool STABLE>
+template <typename K, bool PAIRS>
 __host__ __device__ constexpr size_t scatter_smem_layout(uint32_t B, size_t* off) {
   // offsets: piece_of, cnt, tstart, dbase, stage_key, stage_dst, stage_val, ws
-  using C = ScatterCfg<K, PAIRS, STABLE>;
+  using C = ScatterCfg<K, PAIRS>;
   const uint32_t nid = 2 * B - 1;
   const uint32_t S = (nid + 2) & ~1u;  // counter row stride (entries)
   size_t o = 0;
   off[0] = o; o += (size_t)nid * 2;
   o = (o + 15) & ~(size_t)15;
-  off[1] = o; o += STABLE ? (size_t)C::ROWS * S * 2 : (size_t)S * 4;
+  off[1] = o; o += (size_t)C::W * S * 2;
   off[2] = o; o += (size_t)(nid + 2) * 2;
   o = (o + 15) & ~(size_t)15;
   off[3] = o; o += (size_t)nid * 4;
@@ -51,18 +50,18 @@ __host__ __device__ constexpr size_t scatter_smem_layout(uint32_t B, size_t* off
   return o;
 }
 
-template <typename K, bool PAIRS, bool STABLE>
+// Stable delivery (input order inside every piece).
+template <typename K, bool PAIRS>
 __global__ void __launch_bounds__(256, 2) k_scatter(LevelArgs a) {
-  using Cfg = ScatterCfg<K, PAIRS, STABLE>;
+  using Cfg = ScatterCfg<K, PAIRS>;
   constexpr int NT = Cfg::NT, R = Cfg::R, TILE = Cfg::TILE;
   extern __shared__ __align__(16) unsigned char smem[];
   size_t off[8];
-  scatter_smem_layout<K, PAIRS, STABLE>(a.B, off);
+  scatter_smem_layout<K, PAIRS>(a.B, off);
   const uint32_t nid = a.nid;
   const uint32_t S = (nid + 2) & ~1u;
   uint16_t* piece_of = (uint16_t*)(smem + off[0]);
-  uint16_t* cnt = (uint16_t*)(smem + off[1]);     // STABLE: u16 [warp][piece]
-  uint32_t* cnt32 = (uint32_t*)(smem + off[1]);   // otherwise: u32 [piece]
+  uint16_t* cnt = (uint16_t*)(smem + off[1]);  // [warp][piece]
   uint16_t* tstart = (uint16_t*)(smem + off[2]);
   uint32_t* dbase = (uint32_t*)(smem + off[3]);  // run offset of each piece
   K* stage_key = (K*)(smem + off[4]);
@@ -108,12 +107,10 @@ __global__ void __launch_bounds__(256, 2) k_scatter(LevelArgs a) {
     for (uint32_t t0 = lo; t0 < hi; t0 += TILE) {
       const uint32_t tn = min((uint32_t)TILE, hi - t0);
       // counters of pieces 0..P (P = the dummy piece of the tile's empty slots)
-      if constexpr (STABLE) {
+      {
         const uint32_t hw = (P + 2) / 2;  // 32-bit words per warp row
         for (uint32_t i = tid; i < (uint32_t)Cfg::W * hw; i += NT)
           ((uint32_t*)(cnt + (i / hw) * S))[i % hw] = 0;
-      } else {
-        for (uint32_t i = tid; i <= P; i += NT) cnt32[i] = 0;
       }
       // 1. load keys and ids
       K x[R];
@@ -128,38 +125,27 @@ __global__ void __launch_bounds__(256, 2) k_scatter(LevelArgs a) {
         if constexpr (PAIRS) v[q] = ok ? a.vsrc[t0 + p] : 0ull;
       }
       __syncthreads();
-      uint32_t pk[R];  // piece << 16 | place of the key among the tile's keys of the piece
-      if constexpr (STABLE) {
-        // 2s. rank among the warp's keys of the same piece, in input order
-        uint16_t* crow = cnt + w * S;
+      // 2. rank among the warp's keys of the same piece, in input order
+      uint32_t pk[R];  // piece << 16 | rank among the warp's keys of the piece
+      uint16_t* crow = cnt + w * S;
 #pragma unroll
-        for (int q = 0; q < R; ++q) {
-          const uint32_t p = pc[q] == 0xFFFF ? P : piece_of[pc[q]];
-          const uint32_t peers = __match_any_sync(0xFFFFFFFFu, p);
-          const uint32_t rk = __popc(peers & ltm);
-          const uint32_t base = crow[p];
-          __syncwarp();
-          if (rk == 0) crow[p] = (uint16_t)(base + __popc(peers));
-          __syncwarp();
-          pk[q] = (p << 16) | (base + rk);
-        }
-        __syncthreads();
-        // piece totals, scan over pieces, per-warp starts
-        for (uint32_t p = tid; p <= P; p += NT) {
-          uint32_t s = 0;
+      for (int q = 0; q < R; ++q) {
+        const uint32_t p = pc[q] == 0xFFFF ? P : piece_of[pc[q]];
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, p);
+        const uint32_t rk = __popc(peers & ltm);
+        const uint32_t base = crow[p];
+        __syncwarp();
+        if (rk == 0) crow[p] = (uint16_t)(base + __popc(peers));
+        __syncwarp();
+        pk[q] = (p << 16) | (base + rk);
+      }
+      __syncthreads();
+      // piece totals, scan over pieces, per-warp starts
+      for (uint32_t p = tid; p <= P; p += NT) {
+        uint32_t s = 0;
 #pragma unroll
-          for (int j = 0; j < Cfg::W; ++j) s += cnt[j * S + p];
-          tstart[p] = (uint16_t)s;
-        }
-      } else {
-        // 2a. arrival order: one shared atomic per key
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-          const uint32_t p = pc[q] == 0xFFFF ? P : piece_of[pc[q]];
-          pk[q] = (p << 16) | atomicAdd(&cnt32[p], 1u);
-        }
-        __syncthreads();
-        for (uint32_t p = tid; p <= P; p += NT) tstart[p] = (uint16_t)cnt32[p];
+        for (int j = 0; j < Cfg::W; ++j) s += cnt[j * S + p];
+        tstart[p] = (uint16_t)s;
       }
       __syncthreads();
       {
@@ -178,26 +164,22 @@ __global__ void __launch_bounds__(256, 2) k_scatter(LevelArgs a) {
         if (tid == 0) tstart[m] = (uint16_t)total;
       }
       __syncthreads();
-      if constexpr (STABLE) {
-        for (uint32_t p = tid; p <= P; p += NT) {
-          uint32_t base = tstart[p];
+      for (uint32_t p = tid; p <= P; p += NT) {
+        uint32_t base = tstart[p];
 #pragma unroll
-          for (int j = 0; j < Cfg::W; ++j) {
-            const uint32_t t = cnt[j * S + p];
-            cnt[j * S + p] = (uint16_t)base;
-            base += t;
-          }
+        for (int j = 0; j < Cfg::W; ++j) {
+          const uint32_t t = cnt[j * S + p];
+          cnt[j * S + p] = (uint16_t)base;
+          base += t;
         }
-        __syncthreads();
       }
+      __syncthreads();
       // 3. stage by tile position (piece-major) with the key's destination: piece run
-      //    offset + its place in the piece's tile run
+      //    offset + its place in the piece's tile run (warp start + rank in the warp)
 #pragma unroll
       for (int q = 0; q < R; ++q) {
         const uint32_t pc_ = pk[q] >> 16;
-        const uint32_t place = pk[q] & 0xFFFF;
-        // STABLE: the warp's start in the piece's tile run + rank among the warp's keys
-        const uint32_t pos = (STABLE ? cnt[w * S + pc_] : tstart[pc_]) + place;
+        const uint32_t pos = cnt[w * S + pc_] + (pk[q] & 0xFFFF);
         stage_key[pos] = x[q];
         if (pc_ < P) stage_dst[pos] = dbase[pc_] + (pos - tstart[pc_]);
         if constexpr (PAIRS) stage_val[pos] = v[q];
@@ -215,37 +197,189 @@ __global__ void __launch_bounds__(256, 2) k_scatter(LevelArgs a) {
   }
 }
 
+// ------------------------------------------------------------ keys only, arrival order
+// The same delivery for keys without payloads, with four block barriers per tile:
+// (1) after the per-key atomics, (2) inside the scan of the piece counts, (3) after
+// the scan (which also clears the counts for the next tile), (4) after staging.
+// The next tile's loads and atomics need no barrier before them: the counts were
+// cleared before (3), and the stage arrays and run offsets are next written after
+// the next tile's barrier (3).
+struct ScatterKeysCfg {
+  static constexpr int NT = 256;
+  static constexpr int NW = NT / 32;
+  static constexpr int R = 12;  // keys per thread and tile
+  static constexpr int TILE = NT * R;
+  static constexpr int MINB = 3;  // blocks per SM (80 registers, 65 KB of shared memory)
+};
+
+template <typename K>
+__host__ __device__ constexpr size_t scatter_keys_smem_layout(uint32_t B, size_t* off) {
+  // offsets: piece_of, cnt, tbase, dbase, stage_key, stage_dst, ws
+  using C = ScatterKeysCfg;
+  const uint32_t nid = 2 * B - 1;
+  size_t o = 0;
+  off[0] = o; o += (size_t)nid * 2;
+  o = (o + 15) & ~(size_t)15;
+  off[1] = o; o += (size_t)(nid + 1) * 4;
+  off[2] = o; o += (size_t)(nid + 1) * 4;
+  off[3] = o; o += (size_t)nid * 4;
+  o = (o + 15) & ~(size_t)15;
+  off[4] = o; o += (size_t)C::TILE * sizeof(K);
+  off[5] = o; o += (size_t)C::TILE * 4;
+  off[6] = o; o += (size_t)(C::NW + 1) * 4;
+  return o;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(ScatterKeysCfg::NT, ScatterKeysCfg::MINB) k_scatter_keys(LevelArgs a) {
+  using Cfg = ScatterKeysCfg;
+  constexpr int NT = Cfg::NT, NW = Cfg::NW, R = Cfg::R, TILE = Cfg::TILE;
+  extern __shared__ __align__(16) unsigned char smem[];
+  size_t off[7];
+  scatter_keys_smem_layout<K>(a.B, off);
+  const uint32_t nid = a.nid;
+  uint16_t* piece_of = (uint16_t*)(smem + off[0]);
+  uint32_t* cnt = (uint32_t*)(smem + off[1]);    // keys of each piece in the tile
+  uint32_t* tbase = (uint32_t*)(smem + off[2]);  // tile start of each piece; [P] = tile size
+  uint32_t* dbase = (uint32_t*)(smem + off[3]);  // run offset of each piece
+  K* stage_key = (K*)(smem + off[4]);
+  uint32_t* stage_dst = (uint32_t*)(smem + off[5]);
+  uint32_t* ws = (uint32_t*)(smem + off[6]);
+
+  const uint32_t nseg = a.ctr->nseg;
+  const uint32_t items = a.ctr->items;
+  const K* src = (const K*)a.src;
+  const uint16_t* ids = a.ids;
+  K* dst = (K*)a.dst;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  uint32_t cur_g = 0xFFFFFFFFu;
+  uint32_t P = 0;
+
+  for (uint32_t k = blockIdx.x; k < items; k += gridDim.x) {
+    const uint32_t g = find_seg<&SegInfo::item_off>(a.sinfo, nseg, k);
+    const SegInfo si = a.sinfo[g];
+    const Seg sg = a.segs[g];
+    __syncthreads();  // the previous chunk's last tile is written out
+    if (g != cur_g) {
+      const uint16_t* pof = a.piece_of + (size_t)g * nid;
+      for (uint32_t i = tid; i < nid; i += NT) piece_of[i] = pof[i];
+      P = a.npieces[g];
+      cur_g = g;
+    }
+    const uint32_t* pst = a.piece_start + (size_t)g * nid;
+    for (uint32_t p = tid; p < P; p += NT) {
+      dbase[p] = sg.begin + pst[p];
+      cnt[p] = 0;
+    }
+    __syncthreads();
+    const uint32_t* coff = a.counts + (size_t)k * nid;
+    for (uint32_t i = tid; i < nid; i += NT) {
+      const uint32_t c = coff[i];
+      if (c) atomicAdd(&dbase[piece_of[i]], c);
+    }
+    const uint32_t lo = sg.begin + (k - si.item_off) * a.CH;
+    const uint32_t hi = (uint32_t)min((uint64_t)lo + a.CH, (uint64_t)sg.end);
+    __syncthreads();
+
+    for (uint32_t t0 = lo; t0 < hi; t0 += TILE) {
+      const uint32_t tn = min((uint32_t)TILE, hi - t0);
+      K x[R];
+      uint32_t pk[R];  // piece << 16 | place among the tile's keys of the piece
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const uint32_t i = q * NT + tid;
+        x[q] = i < tn ? order_in<K>(src[t0 + i], a.tf_src) : K(0);
+        pk[q] = i < tn ? ids[t0 + i] : 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        if (q * NT + tid < tn) {
+          const uint32_t p = piece_of[pk[q]];
+          pk[q] = (p << 16) | atomicAdd(&cnt[p], 1u);
+        }
+      }
+      __syncthreads();  // (1)
+      // exclusive scan of cnt[0..P) into tbase, each thread a run of `ch` pieces;
+      // the counts are cleared for the next tile on the way
+      const uint32_t ch = (P + NT - 1) / NT;
+      const uint32_t cb = min(tid * ch, P), ce = min(cb + ch, P);
+      uint32_t s = 0;
+      for (uint32_t i = cb; i < ce; ++i) s += cnt[i];
+      uint32_t inc = s;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= (uint32_t)o) inc += y;
+      }
+      if (lane == 31) ws[w] = inc;
+      __syncthreads();  // (2)
+      uint32_t run = inc - s;
+#pragma unroll
+      for (int j = 0; j < NW; ++j) run += j < (int)w ? ws[j] : 0u;
+      for (uint32_t i = cb; i < ce; ++i) {
+        const uint32_t c = cnt[i];
+        tbase[i] = run;
+        run += c;
+        cnt[i] = 0;
+      }
+      if (tid == 0) tbase[P] = tn;
+      __syncthreads();  // (3)
+      // stage by tile position (piece-major) with the destination: the piece's run
+      // offset + the key's place among the tile's keys of the piece
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        if (q * NT + tid < tn) {
+          const uint32_t p = pk[q] >> 16, place = pk[q] & 0xFFFFu;
+          const uint32_t pos = tbase[p] + place;
+          stage_key[pos] = x[q];
+          stage_dst[pos] = dbase[p] + place;
+        }
+      }
+      __syncthreads();  // (4)
+      for (uint32_t i = tid; i < tn; i += NT) dst[stage_dst[i]] = stage_key[i];
+      for (uint32_t p = tid; p < P; p += NT) dbase[p] += tbase[p + 1] - tbase[p];
+    }
+  }
+}
+
 // ------------------------------------------------------------------------ launchers
 size_t scatter_smem_bytes(int ksize, bool pairs, bool stable, uint32_t B) {
   size_t off[8];
-#define AMS_SZ(K, P, S) return scatter_smem_layout<K, P, S>(B, off)
-  if (ksize == 4) {
-    if (pairs) { if (stable) AMS_SZ(uint32_t, true, true); else AMS_SZ(uint32_t, true, false); }
-    else { if (stable) AMS_SZ(uint32_t, false, true); else AMS_SZ(uint32_t, false, false); }
-  } else {
-    if (pairs) { if (stable) AMS_SZ(uint64_t, true, true); else AMS_SZ(uint64_t, true, false); }
-    else { if (stable) AMS_SZ(uint64_t, false, true); else AMS_SZ(uint64_t, false, false); }
-  }
-#undef AMS_SZ
+  if (!pairs && !stable)
+    return ksize == 4 ? scatter_keys_smem_layout<uint32_t>(B, off) : scatter_keys_smem_layout<uint64_t>(B, off);
+  if (ksize == 4)
+    return pairs ? scatter_smem_layout<uint32_t, true>(B, off) : scatter_smem_layout<uint32_t, false>(B, off);
+  return pairs ? scatter_smem_layout<uint64_t, true>(B, off) : scatter_smem_layout<uint64_t, false>(B, off);
 }
 
 cudaError_t launch_scatter(const LevelArgs& a, int ksize, bool pairs, bool stable, int grid,
                            cudaStream_t s) {
-  const size_t sm = scatter_smem_bytes(ksize, pairs, stable, a.B);
   cudaError_t e;
-#define AMS_LAUNCH_SCATTER(K, P, S)                                                             \
+  if (!pairs && !stable) {
+    const size_t sm = scatter_smem_bytes(ksize, false, false, a.B);
+#define AMS_LAUNCH_KEYS(K)                                                                      \
   do {                                                                                          \
-    e = cudaFuncSetAttribute(k_scatter<K, P, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+    e = cudaFuncSetAttribute(k_scatter_keys<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                              (int)sm);                                                          \
     if (e != cudaSuccess) return e;                                                             \
-    k_scatter<K, P, S><<<grid, 256, sm, s>>>(a);                                                \
+    k_scatter_keys<K><<<grid, ScatterKeysCfg::NT, sm, s>>>(a);                                  \
+  } while (0)
+    if (ksize == 4) AMS_LAUNCH_KEYS(uint32_t); else AMS_LAUNCH_KEYS(uint64_t);
+#undef AMS_LAUNCH_KEYS
+    return cudaGetLastError();
+  }
+  const size_t sm = scatter_smem_bytes(ksize, pairs, true, a.B);
+#define AMS_LAUNCH_SCATTER(K, P)                                                                \
+  do {                                                                                          \
+    e = cudaFuncSetAttribute(k_scatter<K, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                             (int)sm);                                                          \
+    if (e != cudaSuccess) return e;                                                             \
+    k_scatter<K, P><<<grid, 256, sm, s>>>(a);                                                   \
   } while (0)
   if (ksize == 4) {
-    if (pairs) { if (stable) AMS_LAUNCH_SCATTER(uint32_t, true, true); else AMS_LAUNCH_SCATTER(uint32_t, true, false); }
-    else { if (stable) AMS_LAUNCH_SCATTER(uint32_t, false, true); else AMS_LAUNCH_SCATTER(uint32_t, false, false); }
+    if (pairs) AMS_LAUNCH_SCATTER(uint32_t, true); else AMS_LAUNCH_SCATTER(uint32_t, false);
   } else {
-    if (pairs) { if (stable) AMS_LAUNCH_SCATTER(uint64_t, true, true); else AMS_LAUNCH_SCATTER(uint64_t, true, false); }
-    else { if (stable) AMS_LAUNCH_SCATTER(uint64_t, false, true); else AMS_LAUNCH_SCATTER(uint64_t, false, false); }
+    if (pairs) AMS_LAUNCH_SCATTER(uint64_t, true); else AMS_LAUNCH_SCATTER(uint64_t, false);
   }
 #undef AMS_LAUNCH_SCATTER
   return cudaGetLastError();
