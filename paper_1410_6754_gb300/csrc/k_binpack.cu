@@ -20,6 +20,9 @@
 
 namespace ams {
 
+constexpr uint32_t kKeepR = 256;  // largest r whose per-warp group ends stay in shared memory
+constexpr int kCand = 32;          // bounds tried per search round (one warp each)
+
 struct ScanResult {
   uint32_t groups;  // groups formed (stops counting past r)
   uint32_t used;    // largest group formed
@@ -27,33 +30,46 @@ struct ScanResult {
 };
 
 // Scanning algorithm with bound L over prefix sums P[0..B] (P[0] = 0), by one warp.
-__device__ ScanResult warp_scan_groups(const uint32_t* P, uint32_t B, uint32_t r, uint64_t L,
+// A group starting at bucket s ends at the largest e with P[e] - P[s] <= L: lane l
+// holds P[s+1+l], a ballot counts the buckets that fit (they form a prefix of the
+// lanes), and the group's load and the next bucket's prefix come from the same
+// registers -- one shared-memory load per group on the dependent chain.
+__device__ ScanResult warp_scan_groups(const uint32_t* P, uint32_t B, uint32_t r, uint32_t L,
                                        uint32_t* ends) {
   const uint32_t lane = threadIdx.x & 31;
   ScanResult res{0, 0, ~0ull};
-  uint32_t s = 0;
+  uint32_t s = 0, base = P[0];
+  uint32_t win = 1 + lane <= B ? P[1 + lane] : 0u;
   while (s < B) {
     if (res.groups == r) {  // one group too many: infeasible
       res.groups = r + 1;
       break;
     }
     ++res.groups;
-    const uint32_t base = P[s];
-    uint32_t fit = 0;
-    for (uint32_t off = s + 1;; off += 32) {
-      const uint32_t e = off + lane;
-      const bool ok = e <= B && (uint64_t)(P[e] - base) <= L;
-      const uint32_t m = __ballot_sync(0xFFFFFFFFu, ok);
-      const uint32_t c = __popc(m);
-      fit += c;
-      if (c < 32) break;
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, s + 1 + lane <= B && win - base <= L);
+    uint32_t c = __popc(m);  // >= 1: every bucket fits alone
+    uint32_t pe;             // P[s + c]
+    if (c < 32) {
+      pe = __shfl_sync(0xFFFFFFFFu, win, c - 1);
+    } else {  // a group of more than 32 buckets
+      for (uint32_t off = s + 33;; off += 32) {
+        const uint32_t e = off + lane;
+        const uint32_t cc = __popc(__ballot_sync(0xFFFFFFFFu, e <= B && P[e] - base <= L));
+        c += cc;
+        if (cc < 32) break;
+      }
+      pe = P[s + c];
     }
-    const uint32_t e = s + fit;  // >= s+1 because every bucket fits alone
-    const uint32_t load = P[e] - base;
-    res.used = max(res.used, load);
-    if (e < B) res.zmin = min(res.zmin, (uint64_t)(P[e + 1] - base));
+    const uint32_t e = s + c;
+    res.used = max(res.used, pe - base);
+    if (e < B) {
+      const uint32_t pn = c < 32 ? __shfl_sync(0xFFFFFFFFu, win, c) : P[e + 1];
+      res.zmin = min(res.zmin, (uint64_t)(pn - base));
+    }
     if (ends && lane == 0) ends[res.groups - 1] = e;
     s = e;
+    base = pe;
+    win = s + 1 + lane <= B ? P[s + 1 + lane] : 0u;
   }
   return res;
 }
@@ -127,7 +143,8 @@ __global__ void __launch_bounds__(1024) k_binpack(LevelArgs a) {
   __shared__ uint32_t ws[33];
   __shared__ unsigned long long lohi[2];
   __shared__ ScanResult wres[32];
-  __shared__ uint32_t ngroups_s;
+  __shared__ uint32_t ngroups_s, best_s;
+  __shared__ int best_w;
   const uint32_t nseg = a.ctr->nseg;
   const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
 
@@ -155,8 +172,14 @@ __global__ void __launch_bounds__(1024) k_binpack(LevelArgs a) {
     __syncthreads();
     // optimal bound (Section 6 Lemma; Appendix C search).  Every round moves lo up
     // or hi down; 64 rounds cannot be exhausted on valid input (the range starts
-    // below 2^32 and shrinks at least 32-fold per round).  The cap only guards
+    // below 2^32 and shrinks at least kCand-fold per round).  The cap only guards
     // against a logic error: it keeps the feasible hi and flags the status word.
+    // A successful scan at bound c whose largest group is u forms the same groups as
+    // the scan at bound u; so the groups of the scan that set hi last are the groups
+    // at L* when the search ends on that hi (kept when r <= kKeepR, else rescanned).
+    const bool keep = a.r <= kKeepR;
+    uint32_t* wends = ends + a.r;  // kCand slots of r group ends
+    if (tid == 0) best_s = 0xFFFFFFFFu;
     for (int round = 0;; ++round) {
       const uint64_t lo = lohi[0], hi = lohi[1];
       if (lo >= hi) break;
@@ -164,30 +187,52 @@ __global__ void __launch_bounds__(1024) k_binpack(LevelArgs a) {
         __syncthreads();
         if (tid == 0) {
           lohi[0] = hi;
+          best_s = 0xFFFFFFFFu;
           atomicOr(a.status, ST_OVERFLOW);
         }
         __syncthreads();
         break;
       }
-      const uint64_t cand = lo + (hi - lo) * w / 32;
-      const ScanResult rs = warp_scan_groups(P, B, a.r, cand, nullptr);
-      if (lane == 0) wres[w] = rs;
+      if (w < (uint32_t)kCand) {
+        const uint64_t cand = lo + (hi - lo) * w / kCand;
+        const ScanResult rs = warp_scan_groups(P, B, a.r, (uint32_t)cand, keep ? wends + w * a.r : nullptr);
+        if (lane == 0) wres[w] = rs;
+      }
       __syncthreads();
       if (tid == 0) {
         uint64_t nlo = lo, nhi = hi;
-        for (int k = 0; k < 32; ++k) {
-          if (wres[k].groups <= a.r) nhi = min(nhi, (uint64_t)wres[k].used);
-          else nlo = max(nlo, wres[k].zmin);
+        int kbest = -1;
+        for (int k = 0; k < kCand; ++k) {
+          if (wres[k].groups <= a.r) {
+            if ((uint64_t)wres[k].used < nhi) {
+              nhi = wres[k].used;
+              kbest = k;
+            }
+          } else {
+            nlo = max(nlo, wres[k].zmin);
+          }
         }
         lohi[0] = nlo;
         lohi[1] = max(nlo, nhi);
+        best_w = kbest;
+      }
+      __syncthreads();
+      if (keep && best_w >= 0) {  // keep the groups of the new hi
+        const uint32_t ngk = wres[best_w].groups;
+        for (uint32_t i = tid; i < ngk; i += NT) ends[i] = wends[best_w * a.r + i];
+        if (tid == 0) {
+          best_s = (uint32_t)wres[best_w].used;
+          ngroups_s = ngk;
+        }
       }
       __syncthreads();
     }
     const uint64_t Lstar = lohi[0];
-    if (w == 0) {
-      const ScanResult rs = warp_scan_groups(P, B, a.r, Lstar, ends);
-      if (lane == 0) ngroups_s = rs.groups;
+    if (!(keep && best_s == (uint32_t)Lstar)) {
+      if (w == 0) {
+        const ScanResult rs = warp_scan_groups(P, B, a.r, (uint32_t)Lstar, ends);
+        if (lane == 0) ngroups_s = rs.groups;
+      }
     }
     __syncthreads();
     const uint32_t ng = ngroups_s;
@@ -210,7 +255,7 @@ __global__ void __launch_bounds__(1024) k_binpack(LevelArgs a) {
       }
       if (tid == 0) a.npieces[g] = nid;
     } else {
-      uint32_t* pc_s = ends + a.r;  // r counters after the group ends
+      uint32_t* pc_s = ends + a.r;  // r counters after the group ends (over the scan slots)
       for (uint32_t k = tid; k < ng; k += NT) {
         const uint32_t gs = k ? ends[k - 1] : 0, ge = ends[k];
         const uint32_t id_lo = 2 * gs, id_hi = min(2 * ge, nid);
@@ -289,7 +334,9 @@ cudaError_t launch_init(const InitArgs& a, int grid, cudaStream_t s) {
 cudaError_t launch_binpack(const LevelArgs& a, int grid, cudaStream_t s) {
   // dynamic + static shared memory may pass 48 KB even when the dynamic part alone
   // does not, so the limit is always raised to what the launch asks for
-  const size_t sm = (size_t)(a.nid + a.nid + 1 + a.B + 1 + 2 * a.r) * 4;
+  // counts, starts, prefix sums, group ends, and kCand per-warp slots of group ends
+  // (r <= kKeepR) or the per-group piece counters
+  const size_t sm = (size_t)(a.nid + a.nid + 1 + a.B + 1 + a.r + (a.r <= kKeepR ? kCand : 1) * a.r) * 4;
   cudaError_t e = cudaFuncSetAttribute(k_binpack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k_binpack<<<grid, 1024, sm, s>>>(a);

@@ -154,34 +154,48 @@ __global__ void __launch_bounds__(512) k_classify(LevelArgs a) {
 }
 
 // ----------------------------------------------------------------------------- scan
+// One block per (segment, 32 consecutive ids): lane l owns id 32*blk + l and warp w
+// a contiguous range of the segment's chunks (coalesced rows of 32 counts); warp
+// sums, their exclusive prefix over the warps, then the running prefix per warp.
 __global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
+  constexpr int NW = 8;
+  __shared__ uint32_t wsum[NW][32];
   const uint32_t nseg = a.ctr->nseg;
-  const uint32_t nblk = (a.nid + 255) / 256;
+  const uint32_t nid = a.nid;
+  const uint32_t nblk = (nid + 31) / 32;
   const uint32_t total = nseg * nblk;
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (uint32_t p = blockIdx.x; p < total; p += gridDim.x) {
     const uint32_t g = p / nblk;
-    const uint32_t id = (p % nblk) * 256 + threadIdx.x;
-    if (id >= a.nid) continue;
+    const uint32_t id = (p % nblk) * 32 + lane;
     const SegInfo si = a.sinfo[g];
-    uint32_t run = 0;
-    uint32_t* c = a.counts + (size_t)si.item_off * a.nid + id;
-    uint32_t k = 0;
-    for (; k + 4 <= si.nitems; k += 4) {
-      const uint32_t c0 = c[0], c1 = c[a.nid], c2 = c[2 * (size_t)a.nid], c3 = c[3 * (size_t)a.nid];
-      c[0] = run;
-      c[a.nid] = run + c0;
-      c[2 * (size_t)a.nid] = run + c0 + c1;
-      c[3 * (size_t)a.nid] = run + c0 + c1 + c2;
-      run += c0 + c1 + c2 + c3;
-      c += 4 * (size_t)a.nid;
+    const uint32_t per = (si.nitems + NW - 1) / NW;
+    const uint32_t kb = min(w * per, si.nitems), ke = min(kb + per, si.nitems);
+    uint32_t* c = a.counts + (size_t)si.item_off * nid + id;
+    uint32_t s = 0;
+    if (id < nid) {
+#pragma unroll 4
+      for (uint32_t k = kb; k < ke; ++k) s += c[(size_t)k * nid];
     }
-    for (; k < si.nitems; ++k) {
-      const uint32_t c0 = c[0];
-      c[0] = run;
-      run += c0;
-      c += a.nid;
+    wsum[w][lane] = s;
+    __syncthreads();
+    uint32_t run = 0, tot = 0;
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+      const uint32_t v = wsum[j][lane];
+      run += j < (int)w ? v : 0u;
+      tot += v;
     }
-    a.totals[(size_t)g * a.nid + id] = run;
+    if (id < nid) {
+#pragma unroll 4
+      for (uint32_t k = kb; k < ke; ++k) {
+        const uint32_t t = c[(size_t)k * nid];
+        c[(size_t)k * nid] = run;
+        run += t;
+      }
+      if (w == 0) a.totals[(size_t)g * nid + id] = tot;
+    }
+    __syncthreads();
   }
 }
 
