@@ -18,7 +18,7 @@ __all__ = [
     "KT_U32", "KT_U64", "KT_F32",
     "mix64", "splitmix64_outputs", "mulhi64",
     "f32_order", "f32_unorder", "ordered_keys", "unordered_keys",
-    "sort_keys", "sort_pairs", "sort_segmented",
+    "sort_keys", "sort_pairs", "sort_segmented", "select_ranks",
     "stream_key", "sample_indices", "oversampling_factor", "sample",
     "rank_sort", "rank_sort_literal", "splitters", "classify", "classify_literal",
     "bucket_counts", "greedy_groups", "bin_pack", "eq_cut_threshold", "pieces",
@@ -157,6 +157,18 @@ def sort_segmented(kt: int, keys: np.ndarray, offsets: np.ndarray, vals=None):
         if out_v is not None:
             out_v[lo:hi] = np.asarray(vals)[perm]
     return out_k if out_v is None else (out_k, out_v)
+
+
+def select_ranks(kt: int, keys: np.ndarray, ranks) -> np.ndarray:
+    """Output positions ``ranks`` of the keys-only sort, one by one: the value at
+    position i of the definition's output is the i-th smallest T(key) (keys alone
+    carry no index to distinguish equal keys).  numpy's selection (introselect)
+    serves as the library step, so a sampled position of a large sort is checked
+    without sorting it."""
+    ranks = np.asarray(ranks, dtype=np.int64)
+    t = ordered_keys(kt, keys)
+    part = np.partition(t, np.unique(ranks))
+    return unordered_keys(kt, part[ranks])
 
 
 # --------------------------------------------------------------------------------------

@@ -412,3 +412,22 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     # (4) wrong splitter offset j*a-1 changes the closed form
     srt = np.arange(32, dtype=np.uint64)
     assert list(srt[np.arange(1, 8) * 4 - 1]) != list(O.splitters(srt, 4, 8))
+
+
+@pytest.mark.parametrize("kt,bits", [(O.KT_U64, 64), (O.KT_U32, 32), (O.KT_F32, 32)])
+def test_select_ranks_brute_force(kt, bits):
+    """Sampled output positions: the i-th smallest key by brute-force counting on small
+    inputs (rank i is held by the key v with #{x < v} <= i < #{x <= v})."""
+    rng = np.random.default_rng(11)
+    for n in (1, 2, 7, 64, 300):
+        if kt == O.KT_F32:
+            keys = rng.choice(np.array([-2.0, -0.0, 0.0, 1.5, 3.0, -1e30], dtype=np.float32), n)
+            t = O.ordered_keys(kt, keys)
+        else:
+            keys = rng.integers(0, 9, n).astype(np.uint64 if bits == 64 else np.uint32)
+            t = keys.astype(np.uint64)
+        ranks = np.arange(n)
+        got = O.ordered_keys(kt, O.select_ranks(kt, keys, ranks))
+        for i in range(n):
+            v = got[i]
+            assert np.sum(t < v) <= i < np.sum(t <= v)
