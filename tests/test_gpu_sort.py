@@ -162,6 +162,25 @@ def test_out_of_place_and_host_entry_points():
     assert same_bits(h, ek) and np.array_equal(hv, ev)
 
 
+@pytest.mark.parametrize("kt,bits,dist", [(O.KT_U64, 64, "uniform"), (O.KT_U32, 32, "uniform"),
+                                          (O.KT_F32, 32, None), (O.KT_U64, 64, "zipf")])
+@pytest.mark.parametrize("in_off,out_off", [(1, 3), (2, 1), (3, 2)])
+def test_buffers_at_any_element_offset(kt, bits, dist, in_off, out_off):
+    """Input and output views starting at element offsets (so not 16-byte aligned):
+    the levels that write into the caller's buffer handle any 16-byte phase."""
+    n = (1 << 21) + 13
+    keys = I.normal_f32(n, 6) if kt == O.KT_F32 else I.generate(dist, n, 6, bits)
+    big_in = to_dev(np.concatenate([np.zeros(in_off, keys.dtype), keys]))
+    big_out = torch.zeros(n + out_off + 5, dtype=big_in.dtype, device="cuda")
+    src = big_in[in_off:in_off + n]
+    dst = big_out[out_off:out_off + n]
+    ams.sort_keys_into(src, dst, levels=2, buckets=[64, 64], kt=kt)
+    ams.sync()
+    assert same_bits(to_np(dst, keys.dtype), O.sort_keys(kt, keys))
+    rest = torch.cat([big_out[:out_off], big_out[out_off + n:]])
+    assert int((rest != 0).sum().item()) == 0, "wrote outside the output view"
+
+
 def test_contexts_budget_and_errors():
     keys = I.generate("uniform", 1 << 20, 1, 32)
     ctx = ams.Context()
