@@ -59,22 +59,21 @@ __device__ __forceinline__ uint32_t cell_add(uint32_t* cw, uint32_t c) {
   return (atomicAdd(&cw[c >> 1], 1u << sh) >> sh) & 0xFFFFu;
 }
 
-// Cell of key v: d = the top 32 significant bits of v - kmin (a shift by `sh`, done
-// with 32-bit shifts), then c = floor(d * scale / 2^32) -- monotone in v, and below
-// the cell count for every key up to kmax.
+// Cell of key v: d = the top 32 significant bits of v - kmin (a funnel shift by
+// `sh` <= 32 with the shift clamped at 32), then c = floor(d * scale / 2^32) --
+// monotone in v, and below the cell count for every key up to kmax.
 template <typename K>
 struct CellMap {
   K kmin;
-  uint32_t sh;     // (< 32 for 32-bit keys)
+  uint32_t sh;     // 0 for 32-bit keys
   uint32_t scale;
   __device__ __forceinline__ uint32_t operator()(K v) const {
     const K d = (K)(v - kmin);
     uint32_t d32;
     if constexpr (sizeof(K) == 4) {
-      d32 = (uint32_t)d >> sh;
+      d32 = (uint32_t)d;
     } else {
-      const uint32_t lo = (uint32_t)d, hi = (uint32_t)(d >> 32);
-      d32 = sh >= 32 ? hi >> (sh - 32) : __funnelshift_r(lo, hi, sh);
+      d32 = __funnelshift_rc((uint32_t)d, (uint32_t)(d >> 32), sh);
     }
     return __umulhi(d32, scale);
   }
@@ -132,12 +131,9 @@ __device__ __forceinline__ void sort_block(const K* src, K* dst, const uint64_t*
     }
   }
   __syncthreads();  // also: every load is done before any store (src may equal dst)
-  uint32_t hmin = red32[0], hmax = red32[NW];
-#pragma unroll
-  for (int i = 1; i < NW; ++i) {
-    hmin = min(hmin, red32[i]);
-    hmax = max(hmax, red32[NW + i]);
-  }
+  // every warp combines the NW warp results: lane l reads result l % NW
+  const uint32_t hmin = __reduce_min_sync(0xFFFFFFFFu, red32[lane % NW]);
+  const uint32_t hmax = __reduce_max_sync(0xFFFFFFFFu, red32[NW + lane % NW]);
   K kmin, kmax;
   if constexpr (sizeof(K) == 4) {
     kmin = (K)hmin;
@@ -231,9 +227,7 @@ __device__ __forceinline__ void sort_block(const K* src, K* dst, const uint64_t*
     s = __reduce_add_sync(0xFFFFFFFFu, s);
     if (lane == 0) ws[w] = s;
     __syncthreads();
-    uint32_t carry = 0;
-#pragma unroll
-    for (int i = 0; i < NW; ++i) carry += i < (int)w ? ws[i] : 0u;
+    uint32_t carry = __reduce_add_sync(0xFFFFFFFFu, lane < w ? ws[lane] : 0u);  // warps before w
     for (uint32_t i0 = vb; i0 < ve; i0 += 32) {  // (warp-uniform trip count)
       const uint32_t i = i0 + lane;
       uint4 v = i < ve ? cv[i] : make_uint4(0, 0, 0, 0);
@@ -285,11 +279,12 @@ __device__ __forceinline__ void sort_block(const K* src, K* dst, const uint64_t*
       dst[b + cb + r] = order_out<K>(v, tf_out);
       vdst[b + cb + r] = sm.vals[p];
     } else {
-      // (key, slot) order: slots before s count when <= v, slots after when < v
+      // (key, slot) order
 #pragma unroll 1
-      for (uint32_t t = cb; t < s; ++t) r += sm.keys[t] <= v;
-#pragma unroll 1
-      for (uint32_t t = s + 1; t < ce; ++t) r += sm.keys[t] < v;
+      for (uint32_t t = cb; t < ce; ++t) {
+        const K y = sm.keys[t];
+        r += (y < v) | ((y == v) & (t < s));
+      }
       dst[b + cb + r] = order_out<K>(v, tf_out);
     }
   }
