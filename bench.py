@@ -3,7 +3,7 @@
 (r1 = r2 = 256 groups, overpartitioning b = 4), keys/s, per GPU or summed over ranks.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ams|reference]
-                    [--workload two_level_u64|two_level_u64_2e26|single_level_u32]
+                    [--workload two_level_u64|two_level_u64_2e26|segmented_u32|single_level_u32]
 
 One step sorts the whole input once (out of place, so every step sees the same
 unsorted input; the 2 GiB input and output exceed the L2 cache, so no flush is
@@ -37,6 +37,11 @@ WORKLOADS = {
     "two_level_u64_2e26": dict(n=1 << 26, bits=64, kt=1, levels=2, buckets=[256, 64], b=4, a=0,
                                dist="uniform", dtype="u64",
                                desc="2-level AMS-sort, 2^26 uniform uint64 keys, r=256x64, b=4"),
+    # batched segmented sort: 100,000 uint32 segments, log-uniform lengths rescaled to
+    # ~2^28 keys in total, one launch sequence for all segments
+    "segmented_u32": dict(n=1 << 28, bits=32, kt=0, levels=1, buckets=[16], b=4, a=0,
+                          dist="uniform", dtype="u32", segments=100000,
+                          desc="segmented sort, 100,000 uint32 segments (log-uniform lengths, ~2^28 keys)"),
     "single_level_u32": dict(n=1 << 20, bits=32, kt=0, levels=1, buckets=[256], b=1, a=16,
                              dist="uniform", dtype="u32",
                              desc="1-level sample sort, 2^20 uniform uint32 keys, 256 buckets, a=16"),
@@ -171,21 +176,42 @@ def _u64_order(t):
     return t ^ torch.tensor(-(1 << 63), dtype=torch.int64, device=t.device)
 
 
-def _check_sorted(src, dst, bits):
-    """Output sorted and a permutation of the input (order-independent hash)."""
+def _check_sorted(src, dst, bits, offsets=None):
+    """Output sorted (inside every segment) and a permutation of the input (an
+    order-independent hash, per segment when there are segments)."""
     import torch
     from paper_1410_6754_gb300.inputs import _mix_t
     if bits == 64:
-        o = _u64_order(dst)
-        ok = bool((o[1:] >= o[:-1]).all())
-        hs = _mix_t(src).sum()
-        hd = _mix_t(dst).sum()
+        o, oi = _u64_order(dst), src
     else:
-        o = dst.to(torch.int64) & 0xFFFFFFFF
-        ok = bool((o[1:] >= o[:-1]).all())
-        hs = _mix_t(src.to(torch.int64) & 0xFFFFFFFF).sum()
-        hd = _mix_t(o).sum()
-    return ok and bool(hs == hd)
+        o, oi = dst.to(torch.int64) & 0xFFFFFFFF, src.to(torch.int64) & 0xFFFFFFFF
+    if offsets is None:
+        return bool((o[1:] >= o[:-1]).all()) and bool(_mix_t(oi).sum() == _mix_t(o if bits != 64 else dst).sum())
+    lens = offsets[1:] - offsets[:-1]
+    seg = torch.repeat_interleave(torch.arange(lens.numel(), device=dst.device), lens)
+    ok = bool(((o[1:] >= o[:-1]) | (seg[1:] != seg[:-1])).all())
+    z = torch.zeros(lens.numel(), dtype=torch.int64, device=dst.device)
+    hs = z.clone().index_add_(0, seg, _mix_t(oi))
+    hd = z.clone().index_add_(0, seg, _mix_t(o if bits != 64 else dst))
+    return ok and bool(torch.equal(hs, hd))
+
+
+def _plain_per_segment(src, offsets, kw):
+    """Keys/s of sorting every segment with its own plain call (the comparison for the
+    batched segmented sort)."""
+    import torch
+    import paper_1410_6754_gb300 as ams
+    off = offsets.cpu().tolist()
+    dst = torch.empty_like(src)
+    skw = {k: v for k, v in kw.items() if k != "offsets"}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(len(off) - 1):
+        lo, hi = off[s], off[s + 1]
+        if hi > lo:
+            ams.sort_keys_into(src[lo:hi], dst[lo:hi], **skw)
+    torch.cuda.synchronize()
+    return (off[-1] - off[0]) / (time.perf_counter() - t0)
 
 
 def run_ams(args, wl):
@@ -205,14 +231,23 @@ def run_ams(args, wl):
     from paper_1410_6754_gb300 import inputs as I
 
     n, bits = wl["n"], wl["bits"]
+    offsets = None
+    if wl.get("segments"):
+        import numpy as np
+        lens = I.segment_lengths(wl["segments"], n, 4, max_log2=20)
+        off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        n = int(off[-1])
+        offsets = torch.from_numpy(off).cuda()
     src = I.generate(wl["dist"], n, rank, bits, device="cuda")
     dst = torch.empty_like(src)
     ctx = ams.Context()
     kw = dict(levels=wl["levels"], buckets=wl["buckets"], seed=0, a=wl["a"], b=wl["b"], kt=wl["kt"])
+    if offsets is not None:
+        kw["offsets"] = offsets
     for _ in range(args.warmup):
         ctx.sort(src, dst, **kw)
     ctx.sync()
-    if not _check_sorted(src, dst, bits):
+    if not _check_sorted(src, dst, bits, offsets):
         print(json.dumps({"error": "output check failed"}), flush=True)
         return 1
     ctx.stats()  # reset the launch / event tallies
@@ -254,7 +289,7 @@ def run_ams(args, wl):
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None
-    if args.e2e_steps > 0:
+    if args.e2e_steps > 0 and offsets is None:
         host_src = src.cpu().pin_memory()
         host = torch.empty_like(host_src).pin_memory()
         times = []
@@ -273,8 +308,11 @@ def run_ams(args, wl):
                "d2h_bytes_per_step": n * w, "steps": args.e2e_steps,
                "api": "ams_sort_host (pinned host buffers, copies inside the timed region)"}
 
+    plain = None
+    if offsets is not None and rank == 0:
+        plain = _plain_per_segment(src, offsets, kw)
     cpu = None
-    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+    if rank == 0 and world == 1 and args.cpu_seconds > 0 and offsets is None:
         import oracle as O
         m = 1 << 23
         sample = src[:m].cpu().numpy().view("uint64" if bits == 64 else "uint32")
@@ -297,7 +335,9 @@ def run_ams(args, wl):
                        "buckets": wl["buckets"], "b": wl["b"], "a": wl["a"] or "ceil(1.6 log10 n)",
                        "parallelism": f"replicas x{world}",
                        "l2": ("input and output exceed L2; no flush" if n * w > (256 << 20)
-                              else "input fits L2; no flush (not a bench line)")},
+                              else "input fits L2; no flush (not a bench line)"),
+                       **({"segments": wl["segments"], "plain_per_segment_keys_per_s": plain}
+                          if offsets is not None else {})},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": _traffic(dom),
                          "peak_source": f"{peak_src} hbm copy bandwidth",

@@ -88,3 +88,32 @@ def test_pairs_2p27_duplicate_heavy():
 
 def test_pairs_2p27_f32_normal_with_signed_zeros():
     _pairs_check(I.normal_f32(1 << 27, 3), O.KT_F32)
+
+
+def test_segmented_100k_u32():
+    """Batched segmented sort at full size: 100,000 uint32 segments with log-uniform
+    lengths rescaled to ~2^28 keys in total, uniform values, device offsets.  Every
+    segment must come out sorted and hold its own input multiset; a sample of
+    segments is compared with the oracle element by element."""
+    lens = I.segment_lengths(100000, 1 << 28, 4, max_log2=20)
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    n = int(off[-1])
+    keys = I.generate("uniform", n, 4, 32, device="cuda")
+    kin = keys.clone()
+    doff = torch.from_numpy(off).cuda()
+    ams.sort_segmented(keys, doff, levels=1, buckets=[16], kt=O.KT_U32)
+    ams.sync()
+    seg = torch.repeat_interleave(torch.arange(len(lens), device="cuda"), torch.from_numpy(lens).cuda())
+    u = keys.to(torch.int64) & 0xFFFFFFFF
+    ok = (u[1:] >= u[:-1]) | (seg[1:] != seg[:-1])
+    assert bool(ok.all()), "a segment is not sorted"
+    uin = kin.to(torch.int64) & 0xFFFFFFFF
+    h_in = torch.zeros(len(lens), dtype=torch.int64, device="cuda").index_add_(0, seg, I._mix_t(uin))
+    h_out = torch.zeros(len(lens), dtype=torch.int64, device="cuda").index_add_(0, seg, I._mix_t(u))
+    assert torch.equal(h_in, h_out), "a segment does not hold its own keys"
+    rng = np.random.default_rng(4)
+    big = np.argsort(lens)[-3:]
+    for s in np.concatenate([rng.integers(0, len(lens), 20), big]):
+        lo, hi = int(off[s]), int(off[s + 1])
+        want = O.sort_keys(O.KT_U32, kin[lo:hi].cpu().numpy().view(np.uint32))
+        assert np.array_equal(keys[lo:hi].cpu().numpy().view(np.uint32), want)
