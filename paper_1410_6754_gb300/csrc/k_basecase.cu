@@ -19,6 +19,7 @@ struct BaseCfg {
   static constexpr uint32_t CAP = (sizeof(K) == 4 && !PAIRS) ? 16384u : 8192u;
   static constexpr int KPT = CAP / NT;
   static constexpr uint32_t CELLS = 16384;  // 16-bit counters, two per word
+  static constexpr uint32_t BIGCELL = 8;    // cells above this size are checked for one value
   // two blocks per SM when their shared memory fits (keys only)
   static constexpr int MINB = PAIRS ? 1 : 2;
 };
@@ -30,6 +31,8 @@ struct BaseSmem {
   uint16_t* pos;   // input index of each slot (pairs: the stable tiebreak)
   uint64_t* vals;  // payloads by input index
   K* red;          // 3 * (NT/32) keys: min / max, scan totals
+  uint32_t* flag;  // [0]: some cell holds more than BIGCELL keys
+  uint32_t* mixed; // one bit per cell: the cell holds more than one key value
 };
 
 template <typename K, bool PAIRS>
@@ -42,15 +45,18 @@ __host__ __device__ constexpr size_t base_smem_layout(size_t* off) {
   o = (o + 15) & ~(size_t)15;
   off[3] = o; o += PAIRS ? (size_t)C::CAP * 8 : 0;                      // payloads
   off[4] = o; o += (size_t)3 * (C::NT / 32) * sizeof(uint64_t);         // red / scan
+  off[5] = o; o += 16;                                                   // flag
+  off[6] = o; o += (size_t)C::CELLS / 8;                                 // mixed bits
   return o;
 }
 
 template <typename K, bool PAIRS>
 __device__ __forceinline__ BaseSmem<K> base_smem(unsigned char* smem) {
-  size_t off[5];
+  size_t off[7];
   base_smem_layout<K, PAIRS>(off);
   return BaseSmem<K>{(K*)(smem + off[0]), (uint32_t*)(smem + off[1]), (uint16_t*)(smem + off[2]),
-                     (uint64_t*)(smem + off[3]), (K*)(smem + off[4])};
+                     (uint64_t*)(smem + off[3]), (K*)(smem + off[4]), (uint32_t*)(smem + off[5]),
+                     (uint32_t*)(smem + off[6])};
 }
 
 // 16-bit cell counter c (two per 32-bit word; every count, prefix and end is <= CAP)
@@ -198,6 +204,7 @@ __device__ __forceinline__ void sort_block(const K* src, K* dst, const uint64_t*
   const CellMap<K> cell{kmin, sh, scale};
   const uint32_t nv = M / 8;  // 128-bit words of counters
   for (uint32_t i = tid; i < nv; i += NT) ((uint4*)sm.cw)[i] = make_uint4(0, 0, 0, 0);
+  if (tid == 0) sm.flag[0] = 0;
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < KPT; ++q) {
@@ -238,6 +245,9 @@ __device__ __forceinline__ void sort_block(const K* src, K* dst, const uint64_t*
         const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
         if (lane >= (uint32_t)o) inc += y;
       }
+      // largest counter of the word group (16-bit lane-wise maxima)
+      const uint32_t mx = __vmaxu2(__vmaxu2(v.x, v.y), __vmaxu2(v.z, v.w));
+      if (max(mx & 0xFFFFu, mx >> 16) > C::BIGCELL) sm.flag[0] = 1;
       uint32_t run = carry + inc - t;
       auto pre = [&](uint32_t u) {  // word (lo, hi) -> (run, run + lo)
         const uint32_t o = run * 0x10001u + (u << 16);
@@ -264,29 +274,63 @@ __device__ __forceinline__ void sort_block(const K* src, K* dst, const uint64_t*
     }
   }
   __syncthreads();
-  for (uint32_t s = tid; s < m; s += NT) {
-    const K v = sm.keys[s];
-    const uint32_t c = cell(v);
-    const uint32_t cb = c ? c16[c - 1] : 0u, ce = c16[c];
-    uint32_t r = 0;
-    if constexpr (PAIRS) {
-      const uint32_t p = sm.pos[s];
-#pragma unroll 1
-      for (uint32_t t = cb; t < ce; ++t) {
-        const K y = sm.keys[t];
-        r += (y < v) | ((y == v) & (sm.pos[t] < p));
-      }
-      dst[b + cb + r] = order_out<K>(v, tf_out);
-      vdst[b + cb + r] = sm.vals[p];
-    } else {
-      // (key, slot) order
-#pragma unroll 1
-      for (uint32_t t = cb; t < ce; ++t) {
-        const K y = sm.keys[t];
-        r += (y < v) | ((y == v) & (t < s));
-      }
-      dst[b + cb + r] = order_out<K>(v, tf_out);
+  // Cells above BIGCELL keys come from repeated values (equal keys share a cell): if
+  // the item has such cells, mark those holding more than one value; the others are
+  // ranked without comparisons -- by slot for keys only, by input index for pairs.
+  const bool big = sm.flag[0] != 0;
+  if (big) {
+    for (uint32_t i = tid; i < (M + 31) / 32; i += NT) sm.mixed[i] = 0;
+    __syncthreads();
+    for (uint32_t s = tid; s < m; s += NT) {
+      const K v = sm.keys[s];
+      const uint32_t c = cell(v);
+      const uint32_t cb = c ? c16[c - 1] : 0u, ce = c16[c];
+      if (ce - cb > C::BIGCELL && sm.keys[cb] != v) atomicOr(&sm.mixed[c >> 5], 1u << (c & 31));
     }
+    __syncthreads();
+  }
+  auto rank_all = [&](auto one_value_check) {
+    for (uint32_t s = tid; s < m; s += NT) {
+      const K v = sm.keys[s];
+      const uint32_t c = cell(v);
+      const uint32_t cb = c ? c16[c - 1] : 0u, ce = c16[c];
+      const bool one_value = one_value_check(c, ce - cb);
+      uint32_t r = 0;
+      if constexpr (PAIRS) {
+        const uint32_t p = sm.pos[s];
+        if (one_value) {
+#pragma unroll 1
+          for (uint32_t t = cb; t < ce; ++t) r += sm.pos[t] < p;
+        } else {
+#pragma unroll 1
+          for (uint32_t t = cb; t < ce; ++t) {
+            const K y = sm.keys[t];
+            r += (y < v) | ((y == v) & (sm.pos[t] < p));
+          }
+        }
+        dst[b + cb + r] = order_out<K>(v, tf_out);
+        vdst[b + cb + r] = sm.vals[p];
+      } else {
+        if (one_value) {
+          r = s - cb;
+        } else {
+          // (key, slot) order
+#pragma unroll 1
+          for (uint32_t t = cb; t < ce; ++t) {
+            const K y = sm.keys[t];
+            r += (y < v) | ((y == v) & (t < s));
+          }
+        }
+        dst[b + cb + r] = order_out<K>(v, tf_out);
+      }
+    }
+  };
+  if (big) {
+    rank_all([&](uint32_t c, uint32_t len) {
+      return len > C::BIGCELL && !((sm.mixed[c >> 5] >> (c & 31)) & 1u);
+    });
+  } else {
+    rank_all([](uint32_t, uint32_t) { return false; });
   }
 }
 
@@ -378,7 +422,7 @@ __global__ void __launch_bounds__(512) k_bigsort(BaseArgs a) {
 }
 
 size_t basecase_smem_bytes(int ksize, bool pairs) {
-  size_t off[5];
+  size_t off[7];
   if (ksize == 4) return pairs ? base_smem_layout<uint32_t, true>(off) : base_smem_layout<uint32_t, false>(off);
   return pairs ? base_smem_layout<uint64_t, true>(off) : base_smem_layout<uint64_t, false>(off);
 }
