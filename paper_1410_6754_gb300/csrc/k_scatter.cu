@@ -291,10 +291,28 @@ __global__ void __launch_bounds__(ScatterKeysCfg::NT, ScatterKeysCfg::MINB) k_sc
         x[q] = i < tn ? order_in<K>(src[t0 + i], a.tf_src) : K(0);
         pk[q] = i < tn ? ids[t0 + i] : 0u;
       }
+      // one shared atomic per key; when the warp's first 32 keys share a piece
+      // (sorted or duplicate-heavy input), every round whose 32 keys share a piece
+      // takes its 32 places with one atomic
+      bool runs = false;
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        if (q * NT + tid < tn) {
-          const uint32_t p = piece_of[pk[q]];
+        const bool ok = q * NT + tid < tn;
+        const uint32_t p = ok ? piece_of[pk[q]] : 0xFFFFFFFFu;  // (no key: no piece)
+        bool uni = false;
+        uint32_t p0 = 0;
+        if (q == 0 || runs) {  // (warp-uniform)
+          p0 = __shfl_sync(0xFFFFFFFFu, p, 0);
+          uni = __all_sync(0xFFFFFFFFu, p == p0);
+          if (q == 0) runs = uni;
+        }
+        if (uni) {
+          if (p0 != 0xFFFFFFFFu) {  // all 32 lanes hold keys of piece p0
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(&cnt[p0], 32u);
+            pk[q] = (p0 << 16) | (__shfl_sync(0xFFFFFFFFu, base, 0) + lane);
+          }
+        } else if (ok) {
           pk[q] = (p << 16) | atomicAdd(&cnt[p], 1u);
         }
       }
