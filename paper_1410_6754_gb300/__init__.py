@@ -94,6 +94,12 @@ _SIGS = {
     "ams_step_partition": (_ST, [_P, _P, _P, _P, _U64, _I, _P, _U32, _P]),
     "ams_step_base_case": (_ST, [_P, _P, _U64, _I, _P]),
     "ams_sort_small_noalloc": (_ST, [_P, _P, _U64, _I, _P]),
+    "ams_server_create": (_ST, [_U64, _I, _U64, ctypes.POINTER(ctypes.c_void_p)]),
+    "ams_server_submit": (_ST, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "ams_server_wait": (_ST, [_P, _U64, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+    "ams_server_done": (ctypes.c_int, [_P, _U64]),
+    "ams_server_counters": (_ST, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+    "ams_server_destroy": (_ST, [_P]),
     "ams_status_string": (ctypes.c_char_p, [_ST]),
     "ams_default_basecase_cap": (_U32, [_I, _I]),
     "ams_version": (ctypes.c_char_p, []),
@@ -309,6 +315,70 @@ class Context:
         if self.handle:
             _check(lib().ams_context_destroy(self.handle), "ams_context_destroy")
             self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving loop (ams_server_*): submit sort requests on device tensors; they run
+    on the server's worker streams with continuous batching.  The tensors must stay
+    alive and untouched until the request is waited for."""
+
+    def __init__(self, hbm_budget_bytes=0, streams=4, pack_max_keys=1 << 16):
+        self.handle = ctypes.c_void_p()
+        _check(lib().ams_server_create(hbm_budget_bytes, streams, pack_max_keys, ctypes.byref(self.handle)),
+               "ams_server_create")
+        self._keep = {}
+
+    def submit(self, keys_in, keys_out=None, vals_in=None, vals_out=None, levels=2, buckets=(256, 256),
+               seed=0, a=0, b=0, cap=0, kt=None):
+        keys_out = keys_in if keys_out is None else keys_out
+        if vals_in is not None and vals_out is None:
+            vals_out = vals_in
+        bk = _buckets(buckets)
+        rq = Request()
+        rq.keys_in = keys_in.data_ptr()
+        rq.keys_out = keys_out.data_ptr()
+        rq.vals_in = vals_in.data_ptr() if vals_in is not None else None
+        rq.vals_out = vals_out.data_ptr() if vals_out is not None else None
+        rq.d_offsets = None
+        rq.nseg = 1
+        rq.n = keys_in.numel()
+        rq.kt = key_type(keys_in, kt)
+        rq.levels = levels
+        rq.buckets_per_level = ctypes.cast(bk, ctypes.POINTER(ctypes.c_uint32))
+        rq.seed = seed
+        rq.opt = _opts(a, b, cap, 0)
+        t = ctypes.c_uint64()
+        _check(lib().ams_server_submit(self.handle, ctypes.byref(rq), ctypes.byref(t)), "ams_server_submit")
+        self._keep[t.value] = (keys_in, keys_out, vals_in, vals_out)
+        return t.value
+
+    def wait(self, ticket):
+        """Waits for the request; returns (submit_ns, done_ns) host steady-clock times."""
+        t0, t1 = ctypes.c_uint64(), ctypes.c_uint64()
+        st = lib().ams_server_wait(self.handle, ticket, ctypes.byref(t0), ctypes.byref(t1))
+        self._keep.pop(ticket, None)
+        _check(st, "ams_server_wait")
+        return t0.value, t1.value
+
+    def done(self, ticket):
+        return lib().ams_server_done(self.handle, ticket) == 1
+
+    def counters(self):
+        b, p = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().ams_server_counters(self.handle, ctypes.byref(b), ctypes.byref(p)), "ams_server_counters")
+        return {"batches": b.value, "packed_requests": p.value}
+
+    def close(self):
+        if self.handle:
+            _check(lib().ams_server_destroy(self.handle), "ams_server_destroy")
+            self.handle = ctypes.c_void_p()
+            self._keep.clear()
 
     def __del__(self):
         try:

@@ -20,6 +20,7 @@ struct BaseCfg {
   static constexpr int KPT = CAP / NT;
   static constexpr uint32_t CELLS = 16384;  // 16-bit counters, two per word
   static constexpr uint32_t BIGCELL = 8;    // cells above this size are checked for one value
+  static constexpr uint32_t SKEWCELL = 32;  // a cell above this size with two values: bitonic
   // two blocks per SM when their shared memory fits (keys only)
   static constexpr int MINB = PAIRS ? 1 : 2;
 };
@@ -84,6 +85,49 @@ struct CellMap {
     return __umulhi(d32, scale);
   }
 };
+
+// Bitonic sort of the m keys in sm.keys[0, m) (pairs: with their input indices in
+// sm.pos, the tiebreak, so the order stays stable), padded with the largest key to
+// the next power of two, then written to dst[b, b+m) (payloads from sm.vals).
+template <typename K, bool PAIRS>
+__device__ void bitonic_block(K* dst, uint64_t* vdst, uint32_t b, uint32_t m, int tf_out,
+                              const BaseSmem<K>& sm) {
+  using C = BaseCfg<K, PAIRS>;
+  constexpr int NT = C::NT;
+  const uint32_t tid = threadIdx.x;
+  uint32_t mp = 1;
+  while (mp < m) mp <<= 1;
+  for (uint32_t i = m + tid; i < mp; i += NT) {
+    sm.keys[i] = key_max<K>();
+    if constexpr (PAIRS) sm.pos[i] = 0xFFFFu;
+  }
+  __syncthreads();
+  for (uint32_t k = 2; k <= mp; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = tid; i < mp / 2; i += NT) {
+        const uint32_t lo = 2 * i - (i & (j - 1)), hi = lo + j;
+        const bool up = (lo & k) == 0;
+        const K a = sm.keys[lo], c = sm.keys[hi];
+        bool gt = a > c;
+        if constexpr (PAIRS) gt = gt || (a == c && sm.pos[lo] > sm.pos[hi]);
+        if (gt == up) {
+          sm.keys[lo] = c;
+          sm.keys[hi] = a;
+          if constexpr (PAIRS) {
+            const uint16_t t = sm.pos[lo];
+            sm.pos[lo] = sm.pos[hi];
+            sm.pos[hi] = t;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (uint32_t i = tid; i < m; i += NT) {
+    dst[b + i] = order_out<K>(sm.keys[i], tf_out);
+    if constexpr (PAIRS) vdst[b + i] = sm.vals[sm.pos[i]];
+  }
+}
 
 // Sort keys [b, b+m) of `src` (m <= CAP) and write them to `dst` at the same
 // offsets.  tf_in / tf_out: float order map on load / its inverse on store.
@@ -204,7 +248,7 @@ __device__ __forceinline__ void sort_block(const K* src, K* dst, const uint64_t*
   const CellMap<K> cell{kmin, sh, scale};
   const uint32_t nv = M / 8;  // 128-bit words of counters
   for (uint32_t i = tid; i < nv; i += NT) ((uint4*)sm.cw)[i] = make_uint4(0, 0, 0, 0);
-  if (tid == 0) sm.flag[0] = 0;
+  if (tid == 0) sm.flag[0] = sm.flag[1] = 0;
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < KPT; ++q) {
@@ -285,9 +329,19 @@ __device__ __forceinline__ void sort_block(const K* src, K* dst, const uint64_t*
       const K v = sm.keys[s];
       const uint32_t c = cell(v);
       const uint32_t cb = c ? c16[c - 1] : 0u, ce = c16[c];
-      if (ce - cb > C::BIGCELL && sm.keys[cb] != v) atomicOr(&sm.mixed[c >> 5], 1u << (c & 31));
+      if (ce - cb > C::BIGCELL && sm.keys[cb] != v) {
+        atomicOr(&sm.mixed[c >> 5], 1u << (c & 31));
+        if (ce - cb > C::SKEWCELL) sm.flag[1] = 1;
+      }
     }
     __syncthreads();
+    if (sm.flag[1]) {
+      // Keys crowded into few cells with several values (a distribution far from
+      // uniform over [min, max]: ranks in cells would cost the square of the cell
+      // size): bitonic sort of the item, whose cost does not depend on the keys.
+      bitonic_block<K, PAIRS>(dst, vdst, b, m, tf_out, sm);
+      return;
+    }
   }
   auto rank_all = [&](auto one_value_check) {
     for (uint32_t s = tid; s < m; s += NT) {

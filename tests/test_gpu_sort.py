@@ -181,6 +181,17 @@ def test_buffers_at_any_element_offset(kt, bits, dist, in_off, out_off):
     assert int((rest != 0).sum().item()) == 0, "wrote outside the output view"
 
 
+@pytest.mark.parametrize("kt,bits,dist,lg,pairs", [
+    (O.KT_U32, 32, "zipf", 14, False), (O.KT_U32, 32, "zipf", 18, False), (O.KT_U32, 32, "zipf", 18, True),
+    (O.KT_F32, 32, None, 18, False), (O.KT_F32, 32, None, 18, True), (O.KT_U64, 64, "zipf", 20, False)])
+def test_skewed_leaves(kt, bits, dist, lg, pairs):
+    """Leaves whose keys crowd into a few cells with several values (Zipf ranks, float
+    bit patterns near zero) take the distribution-independent path of the base case."""
+    n = 1 << lg
+    keys = I.normal_f32(n, 5) if kt == O.KT_F32 else I.generate(dist, n, 5, bits)
+    _sort_check(keys, kt, 2, [64, 64], pairs=pairs)
+
+
 def test_contexts_budget_and_errors():
     keys = I.generate("uniform", 1 << 20, 1, 32)
     ctx = ams.Context()
