@@ -9,7 +9,7 @@
 //               classify     (bucket ids + per-chunk counts)                Sec. 6, App. D
 //               scan         (per-chunk offsets, per-segment bucket sizes)  Sec. 6
 //               binpack      (optimal grouping, pieces, next-level table)   Sec. 6, App. C
-//               scatter      (stable delivery into the other buffer)        Sec. 6, 4.3
+//               scatter      (delivery into the other buffer; stable for pairs) Sec. 6, 4.3
 //               basecase     (shared-memory sort of this level's leaves)    Sec. 6
 // The host never waits between kernels: every table size lives in device counters
 // and every kernel loops over the work that the counters announce.
