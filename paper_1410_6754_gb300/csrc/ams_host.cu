@@ -67,6 +67,9 @@ ams_status make_plan(uint64_t n, uint64_t nseg_user, ams_key_type kt, bool pairs
     est = (est + rr.back() - 1) / rr.back();
   }
   p->L = (int)rr.size();
+  // every segment holds at most C keys: level 0 hands them all to the base case and
+  // the distribution levels would find no work, so none is launched
+  if (n <= p->C) p->L = 0;
   const uint64_t C = p->C;
   const uint64_t big = n / (C + 1) + 1;  // segments larger than C that fit in n
   p->seg1_cap = std::min<uint64_t>(nseg_user, big);

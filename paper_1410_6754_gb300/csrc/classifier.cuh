@@ -9,7 +9,7 @@
 //           16384 equal-width cells by a monotone cell function; J[c] = #{splitters
 //           whose cell is below c}.  A key's cell bounds j to [J[c], J[c+1]] (every
 //           splitter of a lower cell is smaller than the key, every splitter of a
-//           higher cell larger), and a count over that short span (or, when a
+//           higher cell larger), and a walk over that short span (or, when a
 //           segment has spans above 3, a branch-free binary search with a fixed
 //           number of steps per segment: the widest span of the segment) finishes it.  Cost: one table load plus a few compares instead of
 //           log2(B') dependent loads.
@@ -64,16 +64,28 @@ __device__ __forceinline__ uint32_t table_classify(const uint32_t* J2, const K* 
   const uint32_t jj = J2[cell_of<K>(x, lo, sh)];
   uint32_t base = jj & 0xFFFFu;
   uint32_t len = (jj >> 16) - base;
-  if (steps <= 2) {  // spans of at most 3 splitters: count them
+  if (steps <= 2) {
+    // spans of at most 3 splitters: walk them; the first splitter not below x decides
+    // equality.  Past the span the next splitter lies in a higher cell, so it is
+    // larger than x (no compare needed for the usual empty span).
+    uint32_t eq = 0;
 #pragma unroll 1
-    for (uint32_t i = 0, b0 = base; i < len; ++i) base += spl[b0 + i] < x;
-  } else {
-    for (uint32_t s = 0; s < steps; ++s) {
-      const uint32_t half = len >> 1;
-      const bool lt = len > 0 && spl[base + half] < x;
-      base = lt ? base + half + 1 : base;
-      len = lt ? len - half - 1 : half;
+    for (uint32_t i = 0; i < len; ++i) {
+      const K sp = spl[base];
+      if (sp < x) {
+        ++base;
+      } else {
+        eq = sp == x;
+        break;
+      }
     }
+    return 2 * base + eq;
+  }
+  for (uint32_t s = 0; s < steps; ++s) {
+    const uint32_t half = len >> 1;
+    const bool lt = len > 0 && spl[base + half] < x;
+    base = lt ? base + half + 1 : base;
+    len = lt ? len - half - 1 : half;
   }
   const uint32_t eq = (base < B - 1) && (spl[base] == x);
   return 2 * base + eq;
