@@ -116,6 +116,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x, dist, device):
+    """The largest value of x over all ranks (x itself without a process group)."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, seconds):
+    """Whole-job rate of replicas: every rank processes units_per_rank in `seconds`
+    (the slowest rank's time)."""
+    return world * units_per_rank / seconds
+
+
 def _dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -269,11 +285,8 @@ def run_ams(args, wl):
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     st = ctx.stats()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps * n / (ms * 1e-3)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = job_rate(world, args.steps * n, ms * 1e-3)
 
     # dominant kernel: algorithmic bytes per launch / average launch time
     w = bits // 8
@@ -299,12 +312,8 @@ def run_ams(args, wl):
             t0 = time.perf_counter()
             ams.sort_host(host, **kw)
             times.append(time.perf_counter() - t0)
-        e2e_s = statistics.median(times[1:])
-        if dist:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * n / e2e_s, "unit": "keys/s", "h2d_bytes_per_step": n * w,
+        e2e_s = max_over_ranks(statistics.median(times[1:]), dist, "cuda")
+        e2e = {"value": job_rate(world, n, e2e_s), "unit": "keys/s", "h2d_bytes_per_step": n * w,
                "d2h_bytes_per_step": n * w, "steps": args.e2e_steps,
                "api": "ams_sort_host (pinned host buffers, copies inside the timed region)"}
 
