@@ -412,15 +412,23 @@ def run_serving(args):
             off += int(sizes[i])
     views.sort()
     req = [(kt, pools[kt][o:o + m], outs[kt][o:o + m]) for _, kt, o, m in views]
-    kw = dict(levels=2, buckets=[64, 64])
+    # plan per request: fixed (2 levels, 64 x 64) or the autotuner's per size class
+    # (tuned before the timed runs)
+    plans = []
+    for kt, src, _ in req:
+        if args.tuned:
+            cfg = ams.tune(src.numel(), kt)
+            plans.append(dict(levels=cfg["levels"], buckets=cfg["buckets"], b=cfg["b"]))
+        else:
+            plans.append(dict(levels=2, buckets=[64, 64]))
     # one-at-a-time service times (back to back, warm)
-    for kt, src, dst in req[:20]:
-        ams.sort_keys_into(src, dst, kt=kt, **kw)
+    for i, (kt, src, dst) in enumerate(req[:20]):
+        ams.sort_keys_into(src, dst, kt=kt, **plans[i])
     ams.sync()
     service = np.zeros(N)
     for i, (kt, src, dst) in enumerate(req):
         t0 = time.perf_counter()
-        ams.sort_keys_into(src, dst, kt=kt, **kw)
+        ams.sort_keys_into(src, dst, kt=kt, **plans[i])
         ams.sync()
         service[i] = time.perf_counter() - t0
     rate = 1.1 * N / service.sum()
@@ -433,8 +441,8 @@ def run_serving(args):
     one_tput = sizes.sum() / (done[-1] - arrivals[0])
     # the server on the same stream
     srv = ams.Server(hbm_budget_bytes=64 << 30, streams=args.server_streams, pack_max_keys=1 << 16)
-    for kt, src, dst in req[:20]:  # warm the worker contexts
-        srv.wait(srv.submit(src, dst, kt=kt, **kw))
+    for i, (kt, src, dst) in enumerate(req[:20]):  # warm the worker contexts
+        srv.wait(srv.submit(src, dst, kt=kt, **plans[i]))
     tickets = [None] * N
     t_start = time.monotonic_ns()
 
@@ -445,7 +453,7 @@ def run_serving(args):
                 d = (due - time.monotonic_ns()) / 1e9
                 if d > 2e-4:
                     time.sleep(d - 1e-4)
-            tickets[i] = srv.submit(src, dst, kt=kt, **kw)
+            tickets[i] = srv.submit(src, dst, kt=kt, **plans[i])
 
     th = threading.Thread(target=client)
     th.start()
@@ -469,7 +477,8 @@ def run_serving(args):
         "config": {"workload": f"serving: {N} Poisson requests, sizes log-uniform [2^10, 2^26], "
                                "50% u32 / 30% u64 / 20% f32, uniform or Zipf(1.1) values",
                    "rate_per_s": float(rate), "budget_bytes": 64 << 30, "streams": args.server_streams,
-                   "pack_max_keys": 1 << 16, "levels": 2, "buckets": [64, 64],
+                   "pack_max_keys": 1 << 16,
+                   "plans": "autotuned per size class" if args.tuned else "2 levels, r = 64 x 64",
                    "total_keys": int(sizes.sum())},
         "latency_ms": {"server": {"p50": float(np.percentile(lat_srv, 50)), "p99": float(np.percentile(lat_srv, 99))},
                        "one_at_a_time": {"p50": float(np.percentile(lat_one, 50)),
@@ -492,6 +501,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: request count")
     ap.add_argument("--server-streams", type=int, default=4, help="serving workload: worker streams")
+    ap.add_argument("--tuned", action="store_true", help="serving workload: autotuned plans per size class")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -234,6 +234,23 @@ AMS_API ams_status ams_step_partition(const void* d_in, void* d_out, const uint6
 AMS_API ams_status ams_step_base_case(void* d_keys, uint64_t* d_vals, uint64_t n, ams_key_type kt,
                               void* stream);
 
+/* --------------------------------------------------------------- autotuner
+ * Picks the plan of a size class: for (key type, pairs, ceil(log2 n)) it times a few
+ * candidate plans -- 1, 2 or 3 distribution levels, groups per level r a power of two
+ * near (n / t)^(1/levels) for target leaf sizes t = C/2 and C/4, b = 1 for one level
+ * and 4 otherwise (Section 7 tunes a and b the same way, by measurement) -- on n
+ * synthetic uniform keys in ctx's scratch (ctx NULL = default context), and keeps the
+ * fastest in a table shared by the process (later calls for the class return it at
+ * once).  Allocates and frees 2n keys (and payloads) of device memory per tuning. */
+typedef struct ams_tuned {
+  int levels;
+  uint32_t buckets_per_level[8];  /* r per level, `levels` entries */
+  uint32_t overpartition_b;
+  uint32_t candidates;            /* plans timed */
+  float ms;                       /* time of the chosen plan on the synthetic keys */
+} ams_tuned;
+AMS_API ams_status ams_tune(void* ctx, uint64_t n, ams_key_type kt, int pairs, void* stream, ams_tuned* out);
+
 /* --------------------------------------------------------------- serving loop
  * The paper sorts one input at a time; a server sorts a stream of independent
  * requests of any size and key type with continuous batching.  Requests are

@@ -51,6 +51,12 @@ class Request(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("opt", Options)]
 
 
+class Tuned(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("buckets_per_level", ctypes.c_uint32 * 8),
+                ("overpartition_b", ctypes.c_uint32), ("candidates", ctypes.c_uint32),
+                ("ms", ctypes.c_float)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("levels_planned", ctypes.c_uint32), ("kernel_launches", ctypes.c_uint32),
                 ("segments", ctypes.c_uint32 * 8), ("basecase_items", ctypes.c_uint32 * 9),
@@ -94,6 +100,7 @@ _SIGS = {
     "ams_step_partition": (_ST, [_P, _P, _P, _P, _U64, _I, _P, _U32, _P]),
     "ams_step_base_case": (_ST, [_P, _P, _U64, _I, _P]),
     "ams_sort_small_noalloc": (_ST, [_P, _P, _U64, _I, _P]),
+    "ams_tune": (_ST, [_P, _U64, _I, _I, _P, ctypes.POINTER(Tuned)]),
     "ams_server_create": (_ST, [_U64, _I, _U64, ctypes.POINTER(ctypes.c_void_p)]),
     "ams_server_submit": (_ST, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
     "ams_server_wait": (_ST, [_P, _U64, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
@@ -321,6 +328,16 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def tune(n, kt, pairs=False, ctx=None, stream=None) -> dict:
+    """The autotuner's plan for n keys of type kt (ams_tune): levels, buckets (r per
+    level), b, and its time on synthetic keys."""
+    t = Tuned()
+    h = ctx.handle if ctx is not None else None
+    _check(lib().ams_tune(h, n, kt, 1 if pairs else 0, _stream(stream), ctypes.byref(t)), "ams_tune")
+    return {"levels": t.levels, "buckets": list(t.buckets_per_level)[:t.levels], "b": t.overpartition_b,
+            "candidates": t.candidates, "ms": t.ms}
 
 
 class Server:
