@@ -348,7 +348,8 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
   ln.begin(AMS_K_INIT);
   AMS_TRY(ln.end(launch_init(ia, init_grid, s)));
 
-  const uint64_t bc_grid_cap = (uint64_t)SM * (p.ksize == 4 && !p.pairs ? 1 : 2);
+  // more blocks than fit at once: the block scheduler balances items of uneven size
+  const uint64_t bc_grid_cap = (uint64_t)SM * 8;
   BaseArgs ba{};
   ba.out = rq->keys_out;
   ba.vout = rq->vals_out;
@@ -449,13 +450,13 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
     ln.begin(AMS_K_TABLE);
     AMS_TRY(ln.end(launch_table(la, p.ksize, seg_grid, s)));
     ln.begin(AMS_K_CLASSIFY);
-    AMS_TRY(ln.end(launch_classify(la, p.ksize, tree, SM * 4, s)));
+    AMS_TRY(ln.end(launch_classify(la, p.ksize, tree, SM * 6, s)));
     ln.begin(AMS_K_SCAN);
     AMS_TRY(ln.end(launch_scan(la, SM * 8, s)));
     ln.begin(AMS_K_BINPACK);
     AMS_TRY(ln.end(launch_binpack(la, seg_grid, s)));
     ln.begin(AMS_K_SCATTER);
-    AMS_TRY(ln.end(launch_scatter(la, p.ksize, p.pairs, /*stable=*/p.pairs, SM * (p.pairs ? 2 : 3), s)));
+    AMS_TRY(ln.end(launch_scatter(la, p.ksize, p.pairs, /*stable=*/p.pairs, SM * (p.pairs ? 2 : 6), s)));
     if ((st = run_basecase(la.dst, la.vdst, lb.bc, &b.ctr[l].n_bc, 0, lp.bc_cap, false)) != AMS_OK)
       return st;
     if (la.last && (st = run_basecase(la.dst, la.vdst, b.big, &b.ctr[l].n_big, 0, p.big_cap, true)) != AMS_OK)

@@ -133,9 +133,9 @@ __global__ void __launch_bounds__(512) k_classify(LevelArgs a) {
       count(id);
       ids[pos] = (uint16_t)id;
     }
-    // four 128-bit loads in flight per thread
+    // eight 128-bit loads in flight per thread
     const uint4* vp = (const uint4*)(src + b0);
-    constexpr uint32_t U = 4;
+    constexpr uint32_t U = 8;
     uint32_t v = threadIdx.x;
     for (; v + (U - 1) * NT < nv; v += U * NT) {
       uint4 w[U];
