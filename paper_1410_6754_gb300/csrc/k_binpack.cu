@@ -6,7 +6,7 @@
 //     segment), overwriting the totals table;
 //   * the optimal bound L* of the scanning algorithm over the range-bucket sizes
 //     (equality buckets weigh 0: they are final).  Search of Appendix C: each round
-//     32 warps scan 32 bounds spread over [lo, hi); a successful scan lowers hi to
+//     16 warps scan 16 bounds spread over [lo, hi); a successful scan lowers hi to
 //     the largest group it formed, a failed one raises lo to the smallest
 //     "group + next bucket" load it saw; the answer is lo == hi.  One warp scans
 //     one bound: a group starting at bucket s ends at the largest e with
@@ -21,7 +21,7 @@
 namespace ams {
 
 constexpr uint32_t kKeepR = 256;  // largest r whose per-warp group ends stay in shared memory
-constexpr int kCand = 32;          // bounds tried per search round (one warp each)
+constexpr int kCand = 16;          // bounds tried per search round (one warp each)
 
 struct ScanResult {
   uint32_t groups;  // groups formed (stops counting past r)
@@ -132,8 +132,8 @@ struct Emitter {
   }
 };
 
-__global__ void __launch_bounds__(1024) k_binpack(LevelArgs a) {
-  constexpr int NT = 1024;
+__global__ void __launch_bounds__(512, 2) k_binpack(LevelArgs a) {
+  constexpr int NT = 512;
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t nid = a.nid, B = a.B;
   uint32_t* cnt_s = (uint32_t*)smem;   // nid
@@ -339,7 +339,7 @@ cudaError_t launch_binpack(const LevelArgs& a, int grid, cudaStream_t s) {
   const size_t sm = (size_t)(a.nid + a.nid + 1 + a.B + 1 + a.r + (a.r <= kKeepR ? kCand : 1) * a.r) * 4;
   cudaError_t e = cudaFuncSetAttribute(k_binpack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_binpack<<<grid, 1024, sm, s>>>(a);
+  k_binpack<<<grid, 512, sm, s>>>(a);
   return cudaGetLastError();
 }
 
