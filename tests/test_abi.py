@@ -55,11 +55,34 @@ def test_host_only_calls(libpath):
     assert ams.default_basecase_cap(ams.F32, pairs=True) == 8192
 
 
-def test_struct_layouts_match_header(libpath):
-    # ams_options is 4 uint32; ams_stats layout as declared
-    assert ctypes.sizeof(ams.Options) == 16
-    assert ams.Stats.kernel_ms.offset == 4 + 4 + 32 + 36 + 4 + 4
-    assert ctypes.sizeof(ams.Request) == 8 * 7 + 4 + 4 + 8 + 8 + 16
+def test_struct_layouts_match_header(tmp_path):
+    """ctypes structures against the C compiler's view of include/ams.h (host gcc)."""
+    fields = {
+        "ams_options": (ams.Options, ["oversample_a", "overpartition_b", "basecase_cap", "flags"]),
+        "ams_request": (ams.Request, ["keys_in", "keys_out", "vals_in", "vals_out", "d_offsets", "nseg",
+                                      "n", "kt", "levels", "buckets_per_level", "seed", "opt"]),
+        "ams_stats": (ams.Stats, ["levels_planned", "kernel_launches", "segments", "basecase_items",
+                                  "device_status", "kernel_ms", "kernel_calls", "kernel_elems"]),
+        "ams_tuned": (ams.Tuned, ["levels", "buckets_per_level", "overpartition_b", "candidates", "ms"]),
+    }
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "ams.h"', "int main(void) {"]
+    for st, (_, names) in fields.items():
+        lines.append(f'  printf("{st} size %zu\\n", sizeof({st}));')
+        for f in names:
+            lines.append(f'  printf("{st} {f} %zu\\n", offsetof({st}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.dirname(ams.HEADER), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        parts = ln.split()
+        got[tuple(parts[:-1])] = int(parts[-1])
+    for st, (cls, names) in fields.items():
+        assert got[(st, "size")] == ctypes.sizeof(cls), st
+        for f in names:
+            assert got[(st, f)] == getattr(cls, f).offset, (st, f)
 
 
 def test_built_for_sm103a(libpath):
