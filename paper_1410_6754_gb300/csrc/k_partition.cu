@@ -12,12 +12,14 @@
 namespace ams {
 
 // ---------------------------------------------------------------------------- table
-// J[c] = #{splitters whose cell is below c} = the first splitter index whose cell is
-// >= c (the cells of the sorted splitters do not decrease).
+// Over the D distinct splitter values: J[c] = #{values whose cell is below c} = the
+// first distinct index whose cell is >= c (the cells of the sorted values do not
+// decrease).
 template <typename K>
 __global__ void __launch_bounds__(512) k_table(LevelArgs a) {
   constexpr int NT = 512;
-  __shared__ uint32_t cs[kMaxBuckets];  // cell of every splitter
+  __shared__ uint32_t cs[kMaxBuckets];    // cell of every distinct value
+  __shared__ uint32_t dix[kMaxBuckets];   // distinct index of every splitter
   __shared__ uint32_t ws[NT / 32 + 1];
   const uint32_t nseg = a.ctr->nseg;
   const uint32_t B = a.B, ns = B - 1;
@@ -25,10 +27,15 @@ __global__ void __launch_bounds__(512) k_table(LevelArgs a) {
     const K* spl_g = (const K*)a.spl + (size_t)g * ns;
     const K lo = spl_g[0], hi = spl_g[ns - 1];
     const uint32_t sh = cell_shift<K>(lo, hi);
-    for (uint32_t i = threadIdx.x; i < ns; i += NT) cs[i] = cell_of<K>(spl_g[i], lo, sh);
+    auto starts = [&](uint32_t i) { return i == 0 || spl_g[i] != spl_g[i - 1]; };
+    for (uint32_t i = threadIdx.x; i < ns; i += NT) dix[i] = starts(i) ? 1u : 0u;
     __syncthreads();
-    auto first_at_least = [&](uint32_t c) {  // #{i : cs[i] < c}
-      uint32_t l = 0, h = ns;
+    const uint32_t D = block_scan_array<NT, uint32_t>(dix, ns, ws);
+    for (uint32_t i = threadIdx.x; i < ns; i += NT)
+      if (starts(i)) cs[dix[i]] = cell_of<K>(spl_g[i], lo, sh);
+    __syncthreads();
+    auto first_at_least = [&](uint32_t c) {  // #{d : cs[d] < c}
+      uint32_t l = 0, h = D;
       while (l < h) {
         const uint32_t m = (l + h) >> 1;
         if (cs[m] < c) l = m + 1; else h = m;
@@ -39,7 +46,7 @@ __global__ void __launch_bounds__(512) k_table(LevelArgs a) {
     uint32_t span = 0;
     for (uint32_t c = threadIdx.x; c < kCells; c += NT) {
       const uint32_t j0 = first_at_least(c);
-      const uint32_t j1 = c + 1 == kCells ? ns : first_at_least(c + 1);
+      const uint32_t j1 = c + 1 == kCells ? D : first_at_least(c + 1);
       J2[c] = j0 | (j1 << 16);
       span = max(span, j1 - j0);
     }
@@ -47,8 +54,8 @@ __global__ void __launch_bounds__(512) k_table(LevelArgs a) {
     if (threadIdx.x == 0) {
       ClsHead<K> h;
       h.lo = lo;
-      h.sh = sh;
-      h.steps = mspan ? 32 - __clz((int)mspan) : 0;
+      h.sh_steps = sh | ((mspan ? 32u - __clz((int)mspan) : 0u) << 8);
+      h.D = D;
       ((ClsHead<K>*)a.cls_head)[g] = h;
     }
     __syncthreads();
@@ -63,7 +70,8 @@ __global__ void __launch_bounds__(512) k_classify(LevelArgs a) {
   const uint32_t Bp = 1u << a.logBp;
   ClsSmem<K> cs;
   cls_bind<K>(cs, smem, Bp, TREE);
-  uint32_t* hist = (uint32_t*)(smem + cls_smem_bytes<K>(Bp, TREE));
+  uint32_t* hist = (uint32_t*)(smem + cls_smem_bytes<K>(Bp, TREE));  // (also the loader's scratch)
+  __shared__ uint32_t ws[NT / 32 + 1];
   const uint32_t nseg = a.ctr->nseg;
   const uint32_t items = a.ctr->items;
   const K* src = (const K*)a.src;
@@ -75,8 +83,8 @@ __global__ void __launch_bounds__(512) k_classify(LevelArgs a) {
     const Seg sg = a.segs[g];
     if (g != cur_g) {
       __syncthreads();
-      load_classifier<K>(cs, (const K*)a.spl + (size_t)g * (a.B - 1), (const ClsHead<K>*)a.cls_head + g,
-                         a.J2 + (size_t)g * kCells, a.B, a.logBp, TREE, NT);
+      load_classifier<K, NT>(cs, (const K*)a.spl + (size_t)g * (a.B - 1), (const ClsHead<K>*)a.cls_head + g,
+                             a.J2 + (size_t)g * kCells, a.B, a.logBp, TREE, hist, ws);
       cur_g = g;
     }
     for (uint32_t i = threadIdx.x; i < a.nid; i += NT) hist[i] = 0;
@@ -133,9 +141,9 @@ __global__ void __launch_bounds__(512) k_classify(LevelArgs a) {
       count(id);
       ids[pos] = (uint16_t)id;
     }
-    // eight 128-bit loads in flight per thread
+    // four 128-bit loads in flight per thread
     const uint4* vp = (const uint4*)(src + b0);
-    constexpr uint32_t U = 8;
+    constexpr uint32_t U = 4;
     uint32_t v = threadIdx.x;
     for (; v + (U - 1) * NT < nv; v += U * NT) {
       uint4 w[U];
