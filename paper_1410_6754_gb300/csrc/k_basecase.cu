@@ -1,11 +1,13 @@
 // Base case (Section 6: when the recursion reaches a group that one processing
 // element can sort, it is sorted sequentially).  Here one block sorts one work item:
-//   BC_SORT  up to C keys: load into registers/shared memory, cell_sort, write the
-//            keys (and payloads) at their final positions;
+//   BC_SORT  up to C keys: load into registers, spread over cells in shared memory,
+//            rank within the cells (sort_block; a bitonic network for items whose
+//            keys crowd into few cells), write the keys (and payloads) at their final
+//            positions;
 //   BC_COPY  a final piece (all keys equal, already in input order): copy it to the
 //            output buffer, undoing the float order map if needed;
 //   BC_BIG   a group still larger than C after the last level (only under extreme
-//            skew): sort runs of the block capacity with cell_sort, then merge runs
+//            skew): sort runs of the block capacity with sort_block, then merge runs
 //            pairwise (stable merge path) between the output and a scratch buffer.
 #include <mutex>
 
