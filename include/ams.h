@@ -288,7 +288,8 @@ AMS_API ams_status ams_server_destroy(ams_server* s);
  * ams_sort_keys / ams_sort_pairs, using one thread block: shared-memory sorts of runs
  * and stable pairwise merges.
  *  - n must not exceed AMS_NOALLOC_MAX_KEYS; larger n returns AMS_ERR_INVALID and
- *    touches nothing.  It allocates nothing: the merge scratch is one file-scope
+ *    touches nothing.  So does a d_keys that is not aligned to its key size (4 or 8
+ *    bytes) or a d_vals that is not 8-byte aligned.  It allocates nothing: the merge scratch is one file-scope
  *    device array of AMS_NOALLOC_MAX_KEYS * 16 bytes (8 MiB) that every GPU which
  *    loads the library holds until the process exits.
  *  - The first call on each device looks up that array's device address; make the

@@ -476,7 +476,12 @@ def sort_small_noalloc(keys, vals=None, kt=None, stream=None):
     memory (for callers that cannot allow allocations at call time); its scratch is
     a fixed 8 MiB device array inside the library, shared by all calls on a device,
     so calls must not overlap on the GPU."""
+    kt = key_type(keys, kt)
+    if keys.element_size() != (8 if kt == U64 else 4):
+        raise ValueError("key type does not match the key tensor's element size")
+    if vals is not None and (vals.numel() != keys.numel() or vals.element_size() != 8):
+        raise ValueError("payloads must be one 64-bit value per key")
     _check(lib().ams_sort_small_noalloc(_dev(keys), _dev(vals) if vals is not None else None,
-                                        keys.numel(), key_type(keys, kt), _stream(stream)),
+                                        keys.numel(), kt, _stream(stream)),
            "ams_sort_small_noalloc")
     return keys if vals is None else (keys, vals)

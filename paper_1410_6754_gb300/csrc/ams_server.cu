@@ -221,6 +221,11 @@ void run_loop(ams_server* s) {
       if (wk.jobs.size() > 1) s->packed_requests += wk.jobs.size();
       lk.unlock();
       wk.launch_status = launch(s, wk);
+      // a launch can fail after part of the batch is already queued (a gather copy,
+      // the sort itself): let that work drain before the completion pass hands the
+      // requests back, so no queued copy or kernel touches buffers the caller may
+      // free once its wait returns, and the next batch cannot overwrite the stage
+      if (wk.launch_status != AMS_OK) cudaStreamSynchronize(wk.stream);
       lk.lock();
     }
     if (s->stop && s->queue.empty() && !any_busy) break;

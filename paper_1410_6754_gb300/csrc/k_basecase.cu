@@ -570,6 +570,10 @@ extern "C" AMS_API ams_status ams_sort_small_noalloc(void* d_keys, uint64_t* d_v
   if (n > kNoallocMax) return AMS_ERR_INVALID;  // larger inputs need ams_sort_keys / _pairs
   if (n == 0) return AMS_OK;
   if (!d_keys) return AMS_ERR_INVALID;
+  // the kernel reads and writes whole keys and 64-bit payloads: a misaligned view
+  // would fault on the device, so it is refused here, before any CUDA call
+  const uintptr_t kalign = kt == AMS_U64 ? 8 : 4;
+  if ((uintptr_t)d_keys % kalign != 0 || (uintptr_t)d_vals % 8 != 0) return AMS_ERR_INVALID;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return AMS_ERR_CUDA;
   uint64_t* scratch = nullptr;

@@ -89,3 +89,18 @@ def test_built_for_sm103a(libpath):
     # the fat binary carries sm_103a code (cuobjdump is not used; the build flags are checked)
     assert "arch=compute_103a,code=sm_103a" in " ".join(B.ARCH)
     assert os.path.getsize(libpath) > 100_000
+
+
+def test_noalloc_refuses_misaligned_views_on_the_host(libpath):
+    """ams_sort_small_noalloc checks alignment before any CUDA call: a 64-bit key view
+    at a 4-byte offset, or a payload pointer that is not 8-byte aligned, returns
+    AMS_ERR_INVALID (these addresses are never dereferenced)."""
+    L = ams.lib()
+    p = ctypes.c_void_p
+    assert L.ams_sort_small_noalloc(p(0x10004), None, 10, ams.U64, None) == ams.ERR_INVALID
+    assert L.ams_sort_small_noalloc(p(0x10002), None, 10, ams.U32, None) == ams.ERR_INVALID
+    assert L.ams_sort_small_noalloc(p(0x10000), p(0x20004), 10, ams.U32, None) == ams.ERR_INVALID
+    assert L.ams_sort_small_noalloc(p(0x10000), None, ams.NOALLOC_MAX_KEYS + 1, ams.U32, None) \
+        == ams.ERR_INVALID
+    assert L.ams_sort_small_noalloc(p(0x10000), None, 10, 7, None) == ams.ERR_INVALID
+    assert L.ams_sort_small_noalloc(None, None, 0, ams.U32, None) == ams.OK

@@ -140,6 +140,13 @@ def test_sort_brute_force_f32_specials():
         assert np.array_equal(out_k.view(np.uint32), k.view(np.uint32)[perm])
 
 
+def test_sort_keys_f32_hand_order():
+    """Float keys in float order with -0.0 before +0.0, written out by hand."""
+    k = np.array([1.0, -0.0, float("-inf"), 0.0, -1.0, float("inf"), 1e-45, -1e-45, -1.0], dtype=np.float32)
+    exp = np.array([float("-inf"), -1.0, -1.0, -1e-45, -0.0, 0.0, 1e-45, 1.0, float("inf")], dtype=np.float32)
+    assert np.array_equal(O.sort_keys(O.KT_F32, k).view(np.uint32), exp.view(np.uint32))
+
+
 @pytest.mark.parametrize("kt,bits", [(O.KT_U32, 32), (O.KT_U64, 64)])
 @pytest.mark.parametrize("dist", I.DISTRIBUTIONS)
 def test_sort_invariants(kt, bits, dist):
@@ -394,24 +401,229 @@ def test_single_level_bucket_bound():
     assert tr[0]["counts"][0::2].max() <= 2.5 * n / r
 
 
+# ----------------------------------------------------------------- sample stream
+def test_sample_stream_golden():
+    """Stream states and first draws written by tests/golden/make_sample_stream.py, which
+    implements SplitMix64 in its stateful form with plain Python integers and imports
+    nothing from this repository."""
+    for ln in _lines("sample_stream.txt"):
+        head, idx = ln.split(";")
+        seed, level, begin, n_g, state = head.split()
+        exp = [int(x) for x in idx.split()]
+        assert O.stream_key(int(seed), int(level), int(begin)) == int(state, 16), ln
+        got = O.sample_indices(int(seed), int(level), int(begin), int(n_g), len(exp))
+        assert [int(x) for x in got] == exp, ln
+
+
+def test_a_for_hand_values():
+    """READING of the oversampling factor: ceil(1.6 log10 n_g) (or the fixed a), capped
+    at max(1, n_g // (16 B)).  Values worked by hand."""
+    pl = O.plan(1 << 20, O.KT_U64, 2, [256, 256])
+    assert pl.a_for(1 << 20, 1024) == 10          # 1.6 * 6.02 = 9.63 -> 10; cap 64
+    assert pl.a_for(100000, 1024) == 6            # 1.6 * 5 = 8; cap 100000 // 16384 = 6
+    assert pl.a_for(20000, 1024) == 1             # cap 20000 // 16384 = 1
+    assert pl.a_for(1000, 1024) == 1              # cap max(1, 0) = 1
+    fixed = O.plan(1 << 20, O.KT_U32, 1, [256], b=1, a=16)
+    assert fixed.a_for(1 << 20, 256) == 16        # cap 256
+    assert fixed.a_for(50000, 256) == 12          # cap 50000 // 4096 = 12
+
+
+# ----------------------------------------------------------------- pieces (reading)
+def test_eq_cut_threshold_golden():
+    for ln in _lines("eq_cut_threshold.txt"):
+        L, t = (int(v) for v in ln.split())
+        assert O.eq_cut_threshold(L) == t, ln
+
+
+def _piece_cases():
+    for ln in _lines("pieces_examples.txt"):
+        B, cnt, r, L, ends, begin, pcs, lab = (p.strip() for p in ln.split(";"))
+        yield (int(B), [int(x) for x in cnt.split()], int(r), int(L), [int(x) for x in ends.split()],
+               int(begin), [tuple(int(v) for v in p.split(",")) for p in pcs.split()],
+               [int(x) for x in lab.split()])
+
+
+def test_pieces_golden():
+    """Hand-worked pieces (tests/golden/pieces_examples.txt): the grouping, the final
+    equality pieces (one at a group's end, one at a group's start, two in a row), the
+    dropped empty runs and the per-id labels of the delivery order."""
+    n = 0
+    for B, cnt, r, L, ends, begin, pcs, lab in _piece_cases():
+        gL, ge = O.bin_pack(cnt[0::2], r)
+        assert (gL, ge) == (L, ends)
+        assert O.pieces(np.array(cnt), B, L, ends, begin) == pcs
+        assert list(O.piece_of_ids(np.array(cnt), B, L, ends)) == lab
+        n += 1
+    assert n == 5
+
+
 # ----------------------------------------------------------------- planted mistakes
-def test_pins_catch_planted_mistakes(monkeypatch):
-    """Plausible slips planted in the oracle make one of the pins above fail."""
-    spl = np.array([10, 20, 20, 30], dtype=np.uint64)
-    x = np.array([10, 20, 30], dtype=np.uint64)
-    # (1) '<=' instead of '<' in the splitter count
-    bad = [2 * int(np.searchsorted(spl, v, side="right")) for v in x]
-    assert bad != list(O.classify(spl, 5, x))
-    # (2) binary search upper end one too small
-    w = [3, 1, 4, 1, 5, 9, 2, 6]
-    assert O.greedy_groups(w, 13) is not None and len(O.greedy_groups(w, 13)) > 3
-    # (3) tie-break dropped in the all-pairs rank: ranks stop being a permutation
-    s = np.array([1, 1, 0], dtype=np.uint64)
-    naive = [int((s < v).sum()) for v in s]
-    assert sorted(naive) != [0, 1, 2]
-    # (4) wrong splitter offset j*a-1 changes the closed form
-    srt = np.arange(32, dtype=np.uint64)
-    assert list(srt[np.arange(1, 8) * 4 - 1]) != list(O.splitters(srt, 4, 8))
+import oracle.ams_oracle as _M  # noqa: E402
+
+
+def _bad_classify_le(spl, nbuckets, x):            # '<=' instead of '<' in #{s < x}
+    spl = np.asarray(spl, dtype=np.uint64)
+    x = np.asarray(x, dtype=np.uint64)
+    j = np.searchsorted(spl, x, side="right").astype(np.int64)
+    jj = np.minimum(j, nbuckets - 2)
+    eq = (j < nbuckets - 1) & (spl[jj] == x)
+    return 2 * j + eq.astype(np.int64)
+
+
+def _bad_splitters(sorted_sample, a, nbuckets):    # rank (i+1)a - 1 instead of (i+1)a
+    idx = np.arange(1, nbuckets, dtype=np.int64) * a - 1
+    return np.asarray(sorted_sample, dtype=np.uint64)[idx]
+
+
+def _bad_rank_sort(s, block=512):                  # tie-break dropped
+    s = np.asarray(s, dtype=np.uint64)
+    rank = np.array([(s < v).sum() for v in s], dtype=np.int64)
+    out = np.zeros_like(s)
+    out[np.minimum(rank, len(s) - 1)] = s
+    return rank, out
+
+
+def _bad_bin_pack(w, r):                           # feasible only with fewer than r groups
+    w = [int(x) for x in w]
+    total = sum(w)
+    lo = max((total + r - 1) // r, max(w) if w else 0)
+    hi = max(lo, total)
+    while lo < hi:
+        mid = (lo + hi) // 2
+        e = _M.greedy_groups(w, mid)
+        if e is not None and len(e) < r:
+            hi = mid
+        else:
+            lo = mid + 1
+    return lo, _M.greedy_groups(w, lo)
+
+
+def _bad_stream_key_level(seed, level, begin):    # level instead of level + 1
+    s1 = _M.mix64((seed + level * _M._GAMMA) & _M._M64)
+    return _M.mix64((s1 + (begin + 1) * _M._GAMMA) & _M._M64)
+
+
+def _bad_stream_key_begin(seed, level, begin):    # begin instead of begin + 1
+    s1 = _M.mix64((seed + (level + 1) * _M._GAMMA) & _M._M64)
+    return _M.mix64((s1 + begin * _M._GAMMA) & _M._M64)
+
+
+def _bad_mulhi64(a, b):                            # carry of the middle partial products dropped
+    a = np.asarray(a, dtype=np.uint64)
+    m32, s32 = np.uint64(0xFFFFFFFF), np.uint64(32)
+    bh, bl = np.uint64(int(b) >> 32), np.uint64(int(b) & 0xFFFFFFFF)
+    ah, al = a >> s32, a & m32
+    with np.errstate(over="ignore"):
+        return ah * bh + ((ah * bl) >> s32) + ((al * bh) >> s32)
+
+
+def _bad_eq_cut(L):                                # L*/8 instead of L*/16
+    return max(2, L >> 3)
+
+
+def _bad_pieces(counts, nbuckets, L, ends, begin):  # empty runs kept
+    counts = [int(c) for c in counts]
+    nid = 2 * nbuckets - 1
+    tau = _M.eq_cut_threshold(L)
+    starts = [0] * (nid + 1)
+    for i in range(nid):
+        starts[i + 1] = starts[i] + counts[i]
+    out, g0 = [], 0
+    for e in ends:
+        id_lo, id_hi = 2 * g0, min(2 * e, nid)
+        run = starts[id_lo]
+        for i in range(id_lo, id_hi):
+            if (i & 1) and counts[i] >= tau:
+                out.append((begin + run, begin + starts[i], 0))
+                out.append((begin + starts[i], begin + starts[i + 1], 1))
+                run = starts[i + 1]
+        out.append((begin + run, begin + starts[id_hi], 0))
+        g0 = e
+    return [p for p in out if p[1] > p[0] or p[2] == 0]
+
+
+def _bad_piece_of_ids(counts, nbuckets, L, ends):  # label run not restarted per group
+    counts = [int(c) for c in counts]
+    nid = 2 * nbuckets - 1
+    tau = _M.eq_cut_threshold(L)
+    label = np.zeros(nid, dtype=np.int64)
+    run, g0 = 0, 0
+    for e in ends:
+        for i in range(2 * g0, min(2 * e, nid)):
+            if (i & 1) and counts[i] >= tau:
+                label[i] = i
+                run = i + 1
+            else:
+                label[i] = run
+        g0 = e
+    return label
+
+
+def _bad_sort_keys(kt, keys):                      # float map dropped (raw bit order)
+    keys = np.asarray(keys)
+    raw = keys.view(np.uint32) if keys.dtype == np.float32 else keys
+    return keys[np.argsort(raw, kind="stable")]
+
+
+def _bad_sort_pairs(kt, keys, vals):               # equal keys in reverse index order
+    t = _M.ordered_keys(kt, keys)
+    perm = len(t) - 1 - np.argsort(t[::-1], kind="stable")
+    return np.asarray(keys)[perm], np.asarray(vals)[perm]
+
+
+def _bad_f32_order(bits):                          # negative values not flipped
+    return (np.asarray(bits, dtype=np.uint32) ^ np.uint32(0x80000000)).astype(np.uint32)
+
+
+def _bad_oversampling(n_g):                        # floor instead of ceil
+    return max(1, int(1.6 * np.log10(max(n_g, 1))))
+
+
+def _bad_stable_partition(ids):                    # equal ids in reverse input order
+    ids = np.asarray(ids, dtype=np.int64)
+    return len(ids) - 1 - np.argsort(ids[::-1], kind="stable")
+
+
+def _bad_a_for(self, n_g, nbuckets):               # sample-size cap dropped
+    return self.a if self.a else _M.oversampling_factor(n_g)
+
+
+PLANTED = [
+    # (mistake, oracle attribute, replacement, pin that must fail, pin arguments)
+    ("classify counts splitters <= x", "classify", _bad_classify_le, "test_classify_golden", {}),
+    ("splitter rank shifted by one", "splitters", _bad_splitters, "test_splitters_closed_form", {}),
+    ("rank tie-break dropped", "rank_sort", _bad_rank_sort, "test_rank_sort_against_loops_and_library", {}),
+    ("bin-pack feasibility < r", "bin_pack", _bad_bin_pack, "test_bin_pack_golden", {}),
+    ("stream level offset", "stream_key", _bad_stream_key_level, "test_sample_stream_golden", {}),
+    ("stream begin offset", "stream_key", _bad_stream_key_begin, "test_sample_stream_golden", {}),
+    ("multiply-high carry dropped", "mulhi64", _bad_mulhi64, "test_sample_stream_golden", {}),
+    ("multiply-high carry dropped (exact)", "mulhi64", _bad_mulhi64, "test_mulhi64_against_exact_integers", {}),
+    ("heavy-bucket threshold L/8", "eq_cut_threshold", _bad_eq_cut, "test_eq_cut_threshold_golden", {}),
+    ("empty runs kept as pieces", "pieces", _bad_pieces, "test_pieces_golden", {}),
+    ("piece labels not restarted per group", "piece_of_ids", _bad_piece_of_ids, "test_pieces_golden", {}),
+    ("definition not stable", "sort_pairs", _bad_sort_pairs, "test_sort_brute_force_small_alphabet", {"n": 3}),
+    ("keys sorted by raw float bits", "sort_keys", _bad_sort_keys, "test_sort_keys_f32_hand_order", {}),
+    ("float map without the flip", "f32_order", _bad_f32_order, "test_f32_order_monotone_on_specials", {}),
+    ("oversampling floor", "oversampling_factor", _bad_oversampling, "test_oversampling_factor_closed_form", {}),
+    ("partition not stable", "stable_partition", _bad_stable_partition, "test_ams_restatement_equals_definition",
+     {"dist": "zipf"}),
+    ("a without its cap", "Plan.a_for", _bad_a_for, "test_a_for_hand_values", {}),
+]
+
+
+@pytest.mark.parametrize("what,attr,bad,pin,kw", PLANTED, ids=[p[0] for p in PLANTED])
+def test_pins_catch_planted_mistakes(monkeypatch, what, attr, bad, pin, kw):
+    """A plausible slip planted in the oracle (in its module and in the package's
+    re-export) makes the named pin fail; the unpatched oracle passes the same pin."""
+    pin_fn = globals()[pin]
+    pin_fn(**kw)  # the real oracle passes
+    if attr.startswith("Plan."):
+        monkeypatch.setattr(_M.Plan, attr.split(".")[1], bad)
+    else:
+        monkeypatch.setattr(_M, attr, bad)
+        monkeypatch.setattr(O, attr, bad)
+    with pytest.raises(AssertionError):
+        pin_fn(**kw)
 
 
 @pytest.mark.parametrize("kt,bits", [(O.KT_U64, 64), (O.KT_U32, 32), (O.KT_F32, 32)])

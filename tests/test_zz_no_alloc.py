@@ -9,6 +9,7 @@ collects it last."""
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1410_6754_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -64,3 +65,35 @@ def test_noalloc_rejects_oversize_without_touching_data():
     assert ei.value.status == ams.ERR_INVALID
     torch.cuda.synchronize()
     assert torch.equal(keys, before)
+
+
+@pytest.mark.parametrize("kt", [ams.U32, ams.U64, ams.F32])
+@pytest.mark.parametrize("pairs", [False, True])
+def test_noalloc_edge_sizes_on_a_side_stream(kt, pairs):
+    """n = 1, the one-block capacity C (a single shared-memory sort, no merge) and
+    C + 1 (the smallest merge), enqueued on a non-default stream, against the oracle's
+    (key, original index) order and against the regular sort calls."""
+    cap = ams.default_basecase_cap(kt, pairs)
+    side = torch.cuda.Stream()
+    for n in (1, 2, cap, cap + 1):
+        keys = _inputs(kt, n, 5 + n % 7)
+        vals = np.arange(n, dtype=np.uint64)
+        a_k = _dev(keys)
+        a_v = _dev(vals) if pairs else None
+        torch.cuda.synchronize()
+        with torch.cuda.stream(side):
+            ams.sort_small_noalloc(a_k, a_v, kt=kt, stream=side)
+        side.synchronize()
+        ek, ev = O.sort_pairs(kt, keys, vals)
+        got = a_k.cpu().numpy().view(ek.dtype if kt != ams.F32 else np.float32)
+        assert np.array_equal(got.view(np.uint8), np.ascontiguousarray(ek).view(np.uint8)), (kt, pairs, n)
+        if pairs:
+            assert np.array_equal(a_v.cpu().numpy().view(np.uint64), ev), (kt, pairs, n)
+        b_k = _dev(keys)
+        b_v = _dev(vals) if pairs else None
+        if pairs:
+            ams.sort_pairs(b_k, b_v, levels=2, buckets=[64, 64], kt=kt)
+        else:
+            ams.sort_keys(b_k, levels=2, buckets=[64, 64], kt=kt)
+        torch.cuda.synchronize()
+        assert torch.equal(a_k, b_k), (kt, pairs, n)
