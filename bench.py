@@ -4,12 +4,20 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ams|reference]
                     [--workload two_level_u64|two_level_u64_2e26|segmented_u32|single_level_u32|serving]
+                    [--no-extras]
 
 One step sorts the whole input once (out of place, so every step sees the same
 unsorted input; the 2 GiB input and output exceed the L2 cache, so no flush is
-needed).  Under torchrun every rank sorts its own input (replicas, weak scaling).
-Prints one JSON line on rank 0.  `--impl reference` times the CPU oracle on a
-bounded sample of the same workload instead.
+needed).  The headline is timed without per-kernel events; a second pass with
+events gives the kernel shares.  Under torchrun every rank sorts its own input
+(replicas, weak scaling).  On one GPU the default run appends, to the same JSON line,
+every other configuration of the evaluation: `configs` (ms per sort of the
+single-level 2^20 uint32 sort, the six two-level 2^28 uint64 distributions and the
+two 2^27 pair sorts), `segmented` (100,000 uint32 segments, against one plain call
+per segment) and `serving` (a Poisson stream of mixed requests against the server
+and against one-at-a-time plain sorts replayed at the same arrival times).  Prints
+one JSON line on rank 0.  `--impl reference` times the CPU oracle on a bounded
+sample of the same workload instead.
 """
 from __future__ import annotations
 
@@ -230,6 +238,297 @@ def _plain_per_segment(src, offsets, kw):
     return (off[-1] - off[0]) / (time.perf_counter() - t0)
 
 
+def _cpu_info():
+    """Host cores and CPU model (for the CPU baseline line)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                k = ln.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware") and ":" in ln:
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for ln in out.splitlines():
+                if ln.lower().startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or "unknown"}
+
+
+def _timed(fn, reps, warm=2):
+    """Median ms of fn() over `reps` runs (CUDA events on the current stream, after
+    `warm` untimed runs)."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return statistics.median(times)
+
+
+def run_configs(peak):
+    """ms per sort of every configuration of the evaluation besides the headline
+    (device-resident inputs, out of place, median of 5 after 2 warm-ups), each output
+    checked (sorted and a permutation of its input)."""
+    import numpy as np
+    import torch
+
+    import paper_1410_6754_gb300 as ams
+    from paper_1410_6754_gb300 import inputs as I
+    out = {}
+    ctx = ams.Context()
+
+    def keys_case(name, dist, n, bits, kt, levels, buckets, b, a):
+        src = I.generate(dist, n, 0, bits, device="cuda")
+        dst = torch.empty_like(src)
+        kw = dict(levels=levels, buckets=buckets, seed=0, a=a, b=b, kt=kt)
+        ms = _timed(lambda: ctx.sort(src, dst, **kw), 5)
+        ctx.sync()
+        ok = _check_sorted(src, dst, bits)
+        w = bits // 8
+        alg = (levels + 1) * 2 * n * w
+        out[name] = {"ms": ms, "keys_per_s": n / (ms * 1e-3), "ok": ok,
+                     "step_roofline_frac": alg / (ms * 1e-3) / 1e9 / peak}
+        del src, dst
+
+    def pairs_case(name, keys_np, kt, levels, buckets):
+        n = len(keys_np)
+        dt = torch.int64 if keys_np.dtype == np.uint64 else (torch.float32 if kt == 2 else torch.int32)
+        kin = torch.from_numpy(keys_np.view(np.int64) if keys_np.dtype == np.uint64 else keys_np).cuda()
+        vin = torch.arange(n, dtype=torch.int64, device="cuda")
+        kout, vout = torch.empty_like(kin), torch.empty_like(vin)
+        kw = dict(levels=levels, buckets=buckets, seed=0, kt=kt)
+        ms = _timed(lambda: ctx.sort(kin, kout, vin, vout, **kw), 5)
+        ctx.sync()
+        if kt == 2:
+            bits = kout.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+            t = torch.where(bits >> 31 == 1, bits ^ 0xFFFFFFFF, bits | 0x80000000)
+            same = torch.equal(kout.view(torch.int32), kin.view(torch.int32)[vout])
+        else:
+            t = _u64_order(kout)
+            same = torch.equal(kout, kin[vout])
+        asc = bool(((t[1:] > t[:-1]) | ((t[1:] == t[:-1]) & (vout[1:] > vout[:-1]))).all())
+        w = (8 if kt == 1 else 4) + 8
+        alg = (levels + 1) * 2 * n * w
+        out[name] = {"ms": ms, "pairs_per_s": n / (ms * 1e-3), "ok": bool(same and asc),
+                     "step_roofline_frac": alg / (ms * 1e-3) / 1e9 / peak}
+        del kin, vin, kout, vout
+
+    keys_case("single_level_u32_2e20_uniform_r256_a16", "uniform", 1 << 20, 32, 0, 1, [256], 1, 16)
+    for dist in I.DISTRIBUTIONS:
+        keys_case(f"two_level_u64_2e28_{dist}_r256x256_b4", dist, 1 << 28, 64, 1, 2, [256, 256], 4, 0)
+    pairs_case("pairs_u64_dup1024_2e27_3lvl_r256", I.dup_keys_u64(1 << 27, 2), 1, 3, [256, 256, 256])
+    pairs_case("pairs_f32_normal_zeros_2e27_3lvl_r256", I.normal_f32(1 << 27, 3), 2, 3, [256, 256, 256])
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_segmented_sub(reps=3):
+    """The batched segmented sort (100,000 uint32 segments, log-uniform lengths rescaled
+    to ~2^28 keys, uniform values): one segmented call against one plain call per
+    segment."""
+    import numpy as np
+    import torch
+
+    import paper_1410_6754_gb300 as ams
+    from paper_1410_6754_gb300 import inputs as I
+    wl = WORKLOADS["segmented_u32"]
+    lens = I.segment_lengths(wl["segments"], wl["n"], 4, max_log2=20)
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    n = int(off[-1])
+    offsets = torch.from_numpy(off).cuda()
+    src = I.generate("uniform", n, 0, 32, device="cuda")
+    dst = torch.empty_like(src)
+    ctx = ams.Context()
+    kw = dict(levels=wl["levels"], buckets=wl["buckets"], seed=0, b=wl["b"], kt=0, offsets=offsets)
+    ms = _timed(lambda: ctx.sort(src, dst, **kw), reps)
+    ctx.sync()
+    ok = _check_sorted(src, dst, 32, offsets)
+    plain = _plain_per_segment(src, offsets, kw)
+    ctx.close()
+    del src, dst
+    torch.cuda.empty_cache()
+    return {"segments": wl["segments"], "keys": n, "ms": ms, "keys_per_s": n / (ms * 1e-3),
+            "plain_per_segment_keys_per_s": plain, "ok": ok,
+            "plan": f"levels {wl['levels']}, r {wl['buckets']}, b {wl['b']}; segments <= C go to the base case"}
+
+
+def serving_bench(n_requests, streams, tuned, seed=5):
+    """Serving loop: a seeded Poisson stream of mixed requests (sizes log-uniform in
+    [2^10, 2^26]; key types 50% uint32 / 30% uint64 / 20% float32; uniform or Zipf
+    values, float32 normal) run (a) one at a time, in arrival order, on one stream --
+    each request starts when it has arrived and the previous one has finished -- and
+    (b) through the server (continuous batching over worker streams, 64 GB budget), at
+    the same arrival times.  The arrival rate is 1.1x the one-at-a-time capacity
+    measured on the same requests back to back.  Latency = completion - arrival (host
+    steady clock).  Both runs write separate outputs, which must be equal, sorted and
+    permutations of their inputs."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import paper_1410_6754_gb300 as ams
+    from paper_1410_6754_gb300 import inputs as I
+
+    N = n_requests
+    rng = np.random.default_rng(seed)
+    sizes = np.floor(2.0 ** rng.uniform(10, 26, N)).astype(np.int64)
+    u = rng.random(N)
+    kts = np.where(u < 0.5, 0, np.where(u < 0.8, 1, 2))
+    zipf = rng.random(N) < 0.5
+    pools, outs_one, outs_srv, offs, views = {}, {}, {}, {}, []
+    for kt in (0, 1, 2):
+        idx = np.nonzero(kts == kt)[0]
+        tot = int(sizes[idx].sum())
+        bits = 64 if kt == 1 else 32
+        if kt == 2:
+            base = torch.from_numpy(I.normal_f32(min(tot, 1 << 24), 5).view(np.int32)).cuda()
+            reps = -(-tot // base.numel())
+            pools[kt] = base.repeat(reps)[:tot].contiguous()
+        else:
+            a = I.generate("uniform", tot, 5 + kt, bits, device="cuda")
+            zf = I.generate("zipf", tot, 7 + kt, bits, device="cuda")
+            mask = torch.from_numpy(np.repeat(zipf[idx], sizes[idx])).cuda()
+            pools[kt] = torch.where(mask, zf, a)
+            del a, zf, mask
+        outs_one[kt] = torch.empty_like(pools[kt])
+        outs_srv[kt] = torch.empty_like(pools[kt])
+        off = 0
+        o = [0]
+        for i in idx:
+            views.append((i, kt, off, int(sizes[i])))
+            off += int(sizes[i])
+            o.append(off)
+        offs[kt] = torch.tensor(o, dtype=torch.int64, device="cuda")
+    views.sort()
+    req = [(kt, pools[kt][o:o + m], outs_one[kt][o:o + m], outs_srv[kt][o:o + m]) for _, kt, o, m in views]
+    plans = []
+    t_tune = time.perf_counter()
+    for kt, src, _, _ in req:
+        if tuned:
+            cfg = ams.tune(src.numel(), kt)
+            plans.append(dict(levels=cfg["levels"], buckets=cfg["buckets"], b=cfg["b"]))
+        else:
+            plans.append(dict(levels=2, buckets=[64, 64]))
+    t_tune = time.perf_counter() - t_tune
+    # one-at-a-time service times back to back (warm), for the arrival rate
+    for i, (kt, src, dst, _) in enumerate(req[:20]):
+        ams.sort_keys_into(src, dst, kt=kt, **plans[i])
+    ams.sync()
+    service = np.zeros(N)
+    for i, (kt, src, dst, _) in enumerate(req):
+        t0 = time.perf_counter()
+        ams.sort_keys_into(src, dst, kt=kt, **plans[i])
+        ams.sync()
+        service[i] = time.perf_counter() - t0
+    rate = 1.1 * N / service.sum()
+    arrivals = np.cumsum(np.random.default_rng(seed + 1).exponential(1.0 / rate, N))
+    # (a) one at a time, replayed at the arrival times (measured)
+    done_one = np.zeros(N)
+    t_start = time.perf_counter()
+    for i, (kt, src, dst, _) in enumerate(req):
+        due = t_start + arrivals[i]
+        while time.perf_counter() < due:
+            d = due - time.perf_counter()
+            if d > 2e-4:
+                time.sleep(d - 1e-4)
+        ams.sort_keys_into(src, dst, kt=kt, **plans[i])
+        ams.sync()
+        done_one[i] = time.perf_counter() - t_start
+    lat_one = (done_one - arrivals) * 1e3
+    one_tput = sizes.sum() / (done_one.max() - arrivals[0])
+    # (b) the server on the same stream of arrivals; its worker contexts are sized for
+    # the largest request of the stream first (no allocation inside the timed run)
+    srv = ams.Server(hbm_budget_bytes=64 << 30, streams=streams, pack_max_keys=1 << 16)
+    need = [ams.request_scratch_bytes(int(sizes[i]), int(kts[i]), **plans[i]) for i in range(N)]
+    big = int(np.argmax(need))
+    srv.reserve(int(sizes[big]), int(kts[big]), **plans[big])
+    tickets = [None] * N
+    t_start_ns = time.monotonic_ns()
+
+    def client():
+        for i, (kt, src, _, dst) in enumerate(req):
+            due = t_start_ns + int(arrivals[i] * 1e9)
+            while time.monotonic_ns() < due:
+                d = (due - time.monotonic_ns()) / 1e9
+                if d > 2e-4:
+                    time.sleep(d - 1e-4)
+            tickets[i] = srv.submit(src, dst, kt=kt, **plans[i])
+
+    th = threading.Thread(target=client)
+    th.start()
+    t_done = np.zeros(N)
+    for i in range(N):
+        while tickets[i] is None:
+            time.sleep(1e-5)
+        _, t1 = srv.wait(tickets[i])
+        t_done[i] = (t1 - t_start_ns) / 1e9
+    th.join()
+    counters = srv.counters()
+    srv.close()
+    lat_srv = (t_done - arrivals) * 1e3
+    srv_tput = sizes.sum() / (t_done.max() - arrivals[0])
+    # results: the server's outputs equal the one-at-a-time outputs, which are sorted
+    # per request and hold their request's keys
+    same = all(torch.equal(outs_one[kt], outs_srv[kt]) for kt in pools)
+    sorted_ok = True
+    for kt in pools:
+        if kt == 2:
+            sorted_ok = sorted_ok and _check_sorted_f32(pools[kt], outs_one[kt], offs[kt])
+        else:
+            sorted_ok = sorted_ok and _check_sorted(pools[kt], outs_one[kt], 64 if kt == 1 else 32, offs[kt])
+    res = {
+        "requests": N, "total_keys": int(sizes.sum()), "rate_per_s": float(rate),
+        "budget_bytes": 64 << 30, "streams": streams, "pack_max_keys": 1 << 16,
+        "plans": "autotuned per size class" if tuned else "2 levels, r = 64 x 64",
+        "tune_s": t_tune,
+        "server": {"keys_per_s": float(srv_tput), "p50_ms": float(np.percentile(lat_srv, 50)),
+                   "p99_ms": float(np.percentile(lat_srv, 99))},
+        "one_at_a_time": {"keys_per_s": float(one_tput), "p50_ms": float(np.percentile(lat_one, 50)),
+                          "p99_ms": float(np.percentile(lat_one, 99)),
+                          "how": "measured: requests replayed at the same arrival times, one sort at a time"},
+        "results_equal": bool(same), "results_sorted": bool(sorted_ok),
+        "server_counters": counters,
+    }
+    del pools, outs_one, outs_srv, req
+    torch.cuda.empty_cache()
+    return res
+
+
+def _check_sorted_f32(src, dst, offsets):
+    """Float keys: every segment of dst is in float order (-0.0 before +0.0) and holds
+    the bit patterns of the same segment of src (order-independent hash)."""
+    import torch
+    from paper_1410_6754_gb300.inputs import _mix_t
+
+    def omap(t):
+        b = t.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+        return torch.where(b >> 31 == 1, b ^ 0xFFFFFFFF, b | 0x80000000)
+    o, oi = omap(dst), omap(src)
+    lens = offsets[1:] - offsets[:-1]
+    seg = torch.repeat_interleave(torch.arange(lens.numel(), device=dst.device), lens)
+    ok = bool(((o[1:] >= o[:-1]) | (seg[1:] != seg[:-1])).all())
+    z = torch.zeros(lens.numel(), dtype=torch.int64, device=dst.device)
+    return ok and bool(torch.equal(z.clone().index_add_(0, seg, _mix_t(oi)), z.clone().index_add_(0, seg, _mix_t(o))))
+
+
 def run_ams(args, wl):
     import torch
     rank, world, local_rank = _dist_env()
@@ -273,25 +572,33 @@ def run_ams(args, wl):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    # headline: the sorts alone (no per-kernel events)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
-        ctx.sort(src, dst, flags=ams.FLAG_PHASE_TIMERS, **kw)
+        ctx.sort(src, dst, **kw)
     e1.record()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    st = ctx.stats()
+    st_head = ctx.stats()
     ms = max_over_ranks(ms, dist, "cuda")
     value = job_rate(world, args.steps * n, ms * 1e-3)
+    # kernel shares: a second timed pass with CUDA events around every kernel (on the
+    # stream the kernels are launched on)
+    tsteps = max(3, min(args.steps, 20))
+    for _ in range(tsteps):
+        ctx.sort(src, dst, flags=ams.FLAG_PHASE_TIMERS, **kw)
+    ctx.sync()
+    st = ctx.stats()
 
     # dominant kernel: algorithmic bytes per launch / average launch time
     w = bits // 8
     peak, peak_src = _peaks()
-    calls_per_step = {k: st["kernel_calls"][k] / max(1, args.steps) for k in st["kernel_calls"]}
+    calls_per_step = {k: st["kernel_calls"][k] / max(1, tsteps) for k in st["kernel_calls"]}
     dom = max(KIND_BYTES, key=lambda k: st["kernel_ms"][k])
     avg_ms = st["kernel_ms"][dom] / max(1, st["kernel_calls"][dom])
     bytes_per_launch = KIND_BYTES[dom] * w * st["kernel_elems"][dom] / max(1e-9, calls_per_step[dom])
@@ -316,6 +623,7 @@ def run_ams(args, wl):
         e2e = {"value": job_rate(world, n, e2e_s), "unit": "keys/s", "h2d_bytes_per_step": n * w,
                "d2h_bytes_per_step": n * w, "steps": args.e2e_steps,
                "api": "ams_sort_host (pinned host buffers, copies inside the timed region)"}
+        del host_src, host
 
     plain = None
     if offsets is not None and rank == 0:
@@ -332,7 +640,18 @@ def run_ams(args, wl):
         dt = (time.perf_counter() - t0) / reps
         cpu = {"value": m / dt, "unit": "keys/s", "cores": 1, "kind": "oracle",
                "sample": f"first {m} keys of the same input, numpy stable sort, one thread, "
-                         f"{reps} repetitions"}
+                         f"{reps} repetitions", **_cpu_info()}
+
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras and wl is WORKLOADS["two_level_u64"]:
+        del src, dst
+        ctx.close()
+        torch.cuda.empty_cache()
+        t_ex = time.perf_counter()
+        extras["configs"] = run_configs(peak)
+        extras["segmented"] = run_segmented_sub()
+        extras["serving"] = serving_bench(args.requests, args.server_streams, args.tuned)
+        extras["extras_wall_s"] = time.perf_counter() - t_ex
 
     if rank == 0:
         line = {
@@ -350,14 +669,16 @@ def run_ams(args, wl):
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": _traffic(dom),
                          "peak_source": f"{peak_src} hbm copy bandwidth",
-                         "alg_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms},
+                         "alg_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
+                         "timing": f"per-kernel CUDA events on the launch stream, separate pass of {tsteps} sorts"},
             "step_roofline": {"alg_bytes": step_bytes, "achieved_gbs": step_bytes / (ms / args.steps * 1e-3) / 1e9,
                               "frac": step_bytes / (ms / args.steps * 1e-3) / 1e9 / peak,
                               "definition": "(levels + 1) x (read + write) x n x key bytes per step"},
             "kernel_share": share,
             "kernel_avg_ms": {k: st["kernel_ms"][k] / max(1, st["kernel_calls"][k]) for k in st["kernel_ms"]},
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
-            "gpu_launches": st["kernel_launches"],
+            "gpu_launches": st_head["kernel_launches"],
+            **extras,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -366,125 +687,17 @@ def run_ams(args, wl):
 
 
 def run_serving(args):
-    """Serving loop: a seeded Poisson stream of mixed requests (sizes log-uniform in
-    [2^10, 2^26]; key types 50% uint32 / 30% uint64 / 20% float32; uniform or Zipf
-    values, float32 normal) replayed against the server (continuous batching, 64 GB
-    budget) and against one-at-a-time plain sorts.  The arrival rate is 1.1x the
-    one-at-a-time capacity measured on the same requests back to back; one-at-a-time
-    latencies are the FIFO single-queue replay of those measured service times at the
-    same arrival times.  Latency = completion - arrival (host steady clock)."""
-    import threading
-
-    import numpy as np
-    import torch
-
+    """The serving workload on its own line (see serving_bench)."""
     import __graft_entry__
     __graft_entry__.build()
-    import paper_1410_6754_gb300 as ams
-    from paper_1410_6754_gb300 import inputs as I
-
-    N = args.requests
-    rng = np.random.default_rng(5)
-    sizes = np.floor(2.0 ** rng.uniform(10, 26, N)).astype(np.int64)
-    u = rng.random(N)
-    kts = np.where(u < 0.5, 0, np.where(u < 0.8, 1, 2))
-    zipf = rng.random(N) < 0.5
-    # inputs: one device pool per key type, requests are slices of it
-    pools, outs, views = {}, {}, []
-    for kt in (0, 1, 2):
-        idx = np.nonzero(kts == kt)[0]
-        tot = int(sizes[idx].sum())
-        bits = 64 if kt == 1 else 32
-        if kt == 2:
-            base = torch.from_numpy(I.normal_f32(min(tot, 1 << 26), 5).view(np.int32)).cuda()
-            reps = -(-tot // base.numel())
-            pools[kt] = base.repeat(reps)[:tot].contiguous()
-        else:
-            a = I.generate("uniform", tot, 5 + kt, bits, device="cuda")
-            zf = I.generate("zipf", tot, 7 + kt, bits, device="cuda")
-            mask = torch.from_numpy(np.repeat(zipf[idx], sizes[idx])).cuda()
-            pools[kt] = torch.where(mask, zf, a)
-            del a, zf, mask
-        outs[kt] = torch.empty_like(pools[kt])
-        off = 0
-        for i in idx:
-            views.append((i, kt, off, int(sizes[i])))
-            off += int(sizes[i])
-    views.sort()
-    req = [(kt, pools[kt][o:o + m], outs[kt][o:o + m]) for _, kt, o, m in views]
-    # plan per request: fixed (2 levels, 64 x 64) or the autotuner's per size class
-    # (tuned before the timed runs)
-    plans = []
-    for kt, src, _ in req:
-        if args.tuned:
-            cfg = ams.tune(src.numel(), kt)
-            plans.append(dict(levels=cfg["levels"], buckets=cfg["buckets"], b=cfg["b"]))
-        else:
-            plans.append(dict(levels=2, buckets=[64, 64]))
-    # one-at-a-time service times (back to back, warm)
-    for i, (kt, src, dst) in enumerate(req[:20]):
-        ams.sort_keys_into(src, dst, kt=kt, **plans[i])
-    ams.sync()
-    service = np.zeros(N)
-    for i, (kt, src, dst) in enumerate(req):
-        t0 = time.perf_counter()
-        ams.sort_keys_into(src, dst, kt=kt, **plans[i])
-        ams.sync()
-        service[i] = time.perf_counter() - t0
-    rate = 1.1 * N / service.sum()
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, N))
-    done, t = np.zeros(N), 0.0
-    for i in range(N):
-        t = max(t, arrivals[i]) + service[i]
-        done[i] = t
-    lat_one = (done - arrivals) * 1e3
-    one_tput = sizes.sum() / (done[-1] - arrivals[0])
-    # the server on the same stream
-    srv = ams.Server(hbm_budget_bytes=64 << 30, streams=args.server_streams, pack_max_keys=1 << 16)
-    for i, (kt, src, dst) in enumerate(req[:20]):  # warm the worker contexts
-        srv.wait(srv.submit(src, dst, kt=kt, **plans[i]))
-    tickets = [None] * N
-    t_start = time.monotonic_ns()
-
-    def client():
-        for i, (kt, src, dst) in enumerate(req):
-            due = t_start + int(arrivals[i] * 1e9)
-            while time.monotonic_ns() < due:
-                d = (due - time.monotonic_ns()) / 1e9
-                if d > 2e-4:
-                    time.sleep(d - 1e-4)
-            tickets[i] = srv.submit(src, dst, kt=kt, **plans[i])
-
-    th = threading.Thread(target=client)
-    th.start()
-    t_done = np.zeros(N)
-    for i in range(N):
-        while tickets[i] is None:
-            time.sleep(1e-5)
-        _, t1 = srv.wait(tickets[i])
-        t_done[i] = (t1 - t_start) / 1e9
-    th.join()
-    counters = srv.counters()
-    srv.close()
-    lat_srv = (t_done - arrivals) * 1e3
-    srv_tput = sizes.sum() / (t_done.max() - arrivals[0])
-    # results equal the one-at-a-time sorts' (spot check on a sample)
+    r = serving_bench(args.requests, args.server_streams, args.tuned)
     line = {
-        "metric": METRIC, "value": float(srv_tput), "unit": "keys/s", "n_gpus": 1, "steps": N,
-        "warmup": 20, "ms_per_step": float(1e3 * (t_done.max() - arrivals[0]) / N),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64/f32",
-        "data": "synthetic",
-        "config": {"workload": f"serving: {N} Poisson requests, sizes log-uniform [2^10, 2^26], "
-                               "50% u32 / 30% u64 / 20% f32, uniform or Zipf(1.1) values",
-                   "rate_per_s": float(rate), "budget_bytes": 64 << 30, "streams": args.server_streams,
-                   "pack_max_keys": 1 << 16,
-                   "plans": "autotuned per size class" if args.tuned else "2 levels, r = 64 x 64",
-                   "total_keys": int(sizes.sum())},
-        "latency_ms": {"server": {"p50": float(np.percentile(lat_srv, 50)), "p99": float(np.percentile(lat_srv, 99))},
-                       "one_at_a_time": {"p50": float(np.percentile(lat_one, 50)),
-                                         "p99": float(np.percentile(lat_one, 99))}},
-        "one_at_a_time_keys_per_s": float(one_tput),
-        "server_counters": counters,
+        "metric": METRIC, "value": r["server"]["keys_per_s"], "unit": "keys/s", "n_gpus": 1,
+        "steps": r["requests"], "warmup": 20, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64/f32", "data": "synthetic",
+        "config": {"workload": f"serving: {r['requests']} Poisson requests, sizes log-uniform [2^10, 2^26], "
+                               "50% u32 / 30% u64 / 20% f32, uniform or Zipf(1.1) values"},
+        "serving": r,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -499,7 +712,9 @@ def main():
     ap.add_argument("--workload", default="two_level_u64", choices=sorted(WORKLOADS) + ["serving"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--requests", type=int, default=2000, help="serving workload: request count")
+    ap.add_argument("--requests", type=int, default=400, help="serving: request count")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline only (no configs / segmented / serving sub-objects)")
     ap.add_argument("--server-streams", type=int, default=4, help="serving workload: worker streams")
     ap.add_argument("--tuned", action="store_true", help="serving workload: autotuned plans per size class")
     args = ap.parse_args()

@@ -151,6 +151,16 @@ AMS_API ams_status ams_context_sync(void* ctx);
 /* Bytes of device scratch the context holds now. */
 AMS_API uint64_t ams_context_scratch_bytes(void* ctx);
 
+/* Bytes of device scratch `req` needs in a context (its ping-pong buffer, bucket ids
+ * and per-level tables for the plan the request implies); 0 if the request is
+ * invalid or needs none. */
+AMS_API uint64_t ams_request_scratch_bytes(const ams_request* req);
+
+/* Grow the context's scratch to at least `bytes` now (one cudaMalloc, after waiting for
+ * the device if the context already held scratch), so that later sorts needing at
+ * most that much allocate nothing.  Respects the context's budget (AMS_ERR_OOM). */
+AMS_API ams_status ams_context_reserve(void* ctx, uint64_t bytes);
+
 typedef struct ams_stats {
   uint32_t levels_planned;       /* distribution levels launched */
   uint32_t kernel_launches;      /* kernels launched by the last sort */
@@ -182,6 +192,37 @@ typedef struct ams_stats {
  * kernel_ms and kernel_calls add up every sort since the previous call, which
  * resets them.  ctx NULL = default context. */
 AMS_API ams_status ams_get_stats(void* ctx, ams_stats* out);
+
+/* Intermediates of the context's last sort, per distribution level (for checking the
+ * steps of Section 6 against a restatement; each call waits for that sort).  Segment
+ * `seg` of level `level` (1-based) is one sub-problem sorted at that level: the whole
+ * input at level 1, the non-final pieces above the base-case capacity after that. */
+typedef struct ams_segment_info {
+  uint32_t begin, end;   /* positions [begin, end) of the segment */
+  uint32_t a, S;         /* oversampling factor a and sample size S = a*b*r (Section 6) */
+  uint32_t L, ngroups;   /* optimal group bound L* and groups formed at it (Section 6
+                            Lemma, Appendix C) */
+  uint32_t npieces;      /* delivery pieces: runs of a group's buckets between heavy
+                            equality buckets, and those equality buckets (final) */
+  uint32_t nbucket_ids;  /* 2*b*r - 1 bucket ids of the level */
+} ams_segment_info;
+
+/* *nseg = segments of `level`; the first min(*nseg, max_seg) descriptions go to h_segs
+ * (host, may be NULL), in the device's order (the order groups were emitted in). */
+AMS_API ams_status ams_get_level_segments(void* ctx, int level, uint32_t* nseg,
+                                          ams_segment_info* h_segs, uint32_t max_seg);
+
+/* Tables of segment `seg` of `level` (host arrays, any may be NULL):
+ *  h_bucket_starts (nbucket_ids entries): first position of every bucket id relative to
+ *    the segment's begin (exclusive prefix sum of the global bucket sizes, Section 6);
+ *  h_piece_of (nbucket_ids entries): the piece that delivers each bucket id;
+ *  h_piece_starts (npieces entries): first position of every piece, relative; piece p
+ *    ends where piece p+1 starts (the last at the segment's end).  A piece is final --
+ *    an equality bucket, delivered and never sorted again -- exactly when every id
+ *    mapped to it is odd.  Empty pieces may occur. */
+AMS_API ams_status ams_get_segment_tables(void* ctx, int level, uint32_t seg,
+                                          uint32_t* h_bucket_starts, uint16_t* h_piece_of,
+                                          uint32_t* h_piece_starts);
 
 /* --------------------------------------------------------------- building blocks
  * Each step of one distribution level on one segment, as its own call.  They run the
@@ -258,7 +299,9 @@ AMS_API ams_status ams_tune(void* ctx, uint64_t n, ams_key_type kt, int pairs, v
  * untouched until the request completes).  A host thread owned by the server
  * admits them first come first served while the scratch of the requests in flight
  * stays within hbm_budget_bytes (0 = no limit; a request larger than the whole
- * budget runs alone), runs them on `streams` worker streams (each with its own
+ * budget runs alone) and, when a worker's context would have to grow, while the
+ * device's free memory (cudaMemGetInfo) covers the growth with 256 MiB to spare;
+ * it runs them on `streams` worker streams (each with its own
  * context, kept between requests, so requests overlap on the device), and packs
  * consecutive keys-only requests of one key type of at most pack_max_keys keys each
  * (0 = no packing) into one segmented sort.  Each result is the one the request
@@ -266,6 +309,18 @@ AMS_API ams_status ams_tune(void* ctx, uint64_t n, ams_key_type kt, int pairs, v
 typedef struct ams_server ams_server;
 AMS_API ams_status ams_server_create(uint64_t hbm_budget_bytes, int streams, uint64_t pack_max_keys,
                                      ams_server** out);
+/* The server's admission rule as a pure function (the server loop calls it): with
+ * `in_flight` bytes of scratch held by running requests, a request needing `scratch`
+ * bytes whose worker context would have to grow by `growth` bytes is admitted (1)
+ * when nothing is in flight, or when in_flight + scratch <= budget (0 = no budget)
+ * and growth is 0 or fits in `free_bytes` of free device memory with 256 MiB to
+ * spare; otherwise it waits (0). */
+AMS_API int ams_server_admits(uint64_t in_flight, uint64_t scratch, uint64_t budget, uint64_t growth,
+                              uint64_t free_bytes);
+/* Size every worker context (and the packing stage) for requests up to `largest` now,
+ * so that no allocation -- and no device-wide wait of a reallocation -- happens while
+ * the server runs such requests.  Call before submitting. */
+AMS_API ams_status ams_server_reserve(ams_server* s, const ams_request* largest);
 /* Queue a request (copied; buckets_per_level is copied too); *ticket identifies it. */
 AMS_API ams_status ams_server_submit(ams_server* s, const ams_request* req, uint64_t* ticket);
 /* Block until the request completes; returns its status and, if not NULL, the host

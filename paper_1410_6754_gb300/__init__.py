@@ -51,6 +51,12 @@ class Request(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("opt", Options)]
 
 
+class SegmentInfo(ctypes.Structure):
+    _fields_ = [("begin", ctypes.c_uint32), ("end", ctypes.c_uint32), ("a", ctypes.c_uint32),
+                ("S", ctypes.c_uint32), ("L", ctypes.c_uint32), ("ngroups", ctypes.c_uint32),
+                ("npieces", ctypes.c_uint32), ("nbucket_ids", ctypes.c_uint32)]
+
+
 class Tuned(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("buckets_per_level", ctypes.c_uint32 * 8),
                 ("overpartition_b", ctypes.c_uint32), ("candidates", ctypes.c_uint32),
@@ -91,7 +97,11 @@ _SIGS = {
     "ams_sort_request": (_ST, [_P, ctypes.POINTER(Request), _P]),
     "ams_context_sync": (_ST, [_P]),
     "ams_context_scratch_bytes": (_U64, [_P]),
+    "ams_request_scratch_bytes": (_U64, [ctypes.POINTER(Request)]),
+    "ams_context_reserve": (_ST, [_P, _U64]),
     "ams_get_stats": (_ST, [_P, ctypes.POINTER(Stats)]),
+    "ams_get_level_segments": (_ST, [_P, _I, _PU32, ctypes.POINTER(SegmentInfo), _U32]),
+    "ams_get_segment_tables": (_ST, [_P, _I, _U32, _P, _P, _P]),
     "ams_step_sample": (_ST, [_P, _U64, _I, _U32, _U64, _U32, _U64, _P, _P]),
     "ams_step_rank_sort": (_ST, [_P, _U32, _I, _P, _P]),
     "ams_step_splitters": (_ST, [_P, _U32, _U32, _I, _P, _P]),
@@ -102,6 +112,8 @@ _SIGS = {
     "ams_sort_small_noalloc": (_ST, [_P, _P, _U64, _I, _P]),
     "ams_tune": (_ST, [_P, _U64, _I, _I, _P, ctypes.POINTER(Tuned)]),
     "ams_server_create": (_ST, [_U64, _I, _U64, ctypes.POINTER(ctypes.c_void_p)]),
+    "ams_server_reserve": (_ST, [_P, ctypes.POINTER(Request)]),
+    "ams_server_admits": (ctypes.c_int, [_U64, _U64, _U64, _U64, _U64]),
     "ams_server_submit": (_ST, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
     "ams_server_wait": (_ST, [_P, _U64, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "ams_server_done": (ctypes.c_int, [_P, _U64]),
@@ -318,6 +330,29 @@ class Context:
     def scratch_bytes(self):
         return int(lib().ams_context_scratch_bytes(self.handle))
 
+    def reserve(self, nbytes):
+        """Grow the context's scratch to at least nbytes now (ams_context_reserve)."""
+        _check(lib().ams_context_reserve(self.handle, int(nbytes)), "ams_context_reserve")
+
+    def level_segments(self, level):
+        """Segments sorted at distribution level `level` (1-based) by the last sort, with
+        their a, S, L*, groups and pieces (ams_get_level_segments)."""
+        n = ctypes.c_uint32()
+        _check(lib().ams_get_level_segments(self.handle, level, ctypes.byref(n), None, 0),
+               "ams_get_level_segments")
+        arr = (SegmentInfo * max(1, n.value))()
+        _check(lib().ams_get_level_segments(self.handle, level, ctypes.byref(n), arr, n.value),
+               "ams_get_level_segments")
+        return [{f: getattr(arr[i], f) for f, _ in SegmentInfo._fields_} for i in range(n.value)]
+
+    def segment_tables(self, level, seg, nbucket_ids, npieces):
+        """(bucket starts, piece of every id, piece starts) of one segment, as lists."""
+        bs = (ctypes.c_uint32 * nbucket_ids)()
+        po = (ctypes.c_uint16 * nbucket_ids)()
+        ps = (ctypes.c_uint32 * max(1, npieces))()
+        _check(lib().ams_get_segment_tables(self.handle, level, seg, bs, po, ps), "ams_get_segment_tables")
+        return list(bs), list(po), list(ps)[:npieces]
+
     def close(self):
         if self.handle:
             _check(lib().ams_context_destroy(self.handle), "ams_context_destroy")
@@ -328,6 +363,29 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def _sizing_request(n, kt, levels, buckets, a=0, b=0, cap=0, pairs=False, nseg=1):
+    """A request description for sizing only (no buffers: the size calls read n, the
+    key type, the plan parameters and whether there are payloads or segments)."""
+    bk = _buckets(buckets)
+    rq = Request()
+    rq.keys_in = rq.keys_out = 16
+    rq.vals_in = rq.vals_out = 16 if pairs else None
+    rq.d_offsets = 16 if nseg > 1 else None
+    rq.nseg = nseg
+    rq.n = n
+    rq.kt = kt
+    rq.levels = levels
+    rq.buckets_per_level = ctypes.cast(bk, ctypes.POINTER(ctypes.c_uint32))
+    rq.opt = _opts(a, b, cap, 0)
+    return rq, bk
+
+
+def request_scratch_bytes(n, kt, levels=2, buckets=(256, 256), a=0, b=0, cap=0, pairs=False, nseg=1) -> int:
+    """Device scratch a sort of this shape needs in a context (ams_request_scratch_bytes)."""
+    rq, _bk = _sizing_request(n, kt, levels, buckets, a, b, cap, pairs, nseg)
+    return int(lib().ams_request_scratch_bytes(ctypes.byref(rq)))
 
 
 def tune(n, kt, pairs=False, ctx=None, stream=None) -> dict:
@@ -350,6 +408,11 @@ class Server:
         _check(lib().ams_server_create(hbm_budget_bytes, streams, pack_max_keys, ctypes.byref(self.handle)),
                "ams_server_create")
         self._keep = {}
+
+    def reserve(self, n, kt, levels=2, buckets=(256, 256), a=0, b=0, cap=0, pairs=False):
+        """Size every worker for requests up to this shape now (ams_server_reserve)."""
+        rq, _bk = _sizing_request(n, kt, levels, buckets, a, b, cap, pairs)
+        _check(lib().ams_server_reserve(self.handle, ctypes.byref(rq)), "ams_server_reserve")
 
     def submit(self, keys_in, keys_out=None, vals_in=None, vals_out=None, levels=2, buckets=(256, 256),
                seed=0, a=0, b=0, cap=0, kt=None):

@@ -750,6 +750,28 @@ ams_status ams_context_sync(void* ctx) {
   return read_status(cx);
 }
 
+uint64_t ams_request_scratch_bytes(const ams_request* rq) {
+  if (!rq || rq->n == 0 || rq->n >= 0xFFFFFFFFull) return 0;
+  const bool pairs = rq->vals_in != nullptr;
+  const uint64_t nseg_user = rq->d_offsets ? rq->nseg : 1;
+  if (nseg_user == 0) return 0;
+  int sm = 148;
+  Context* cx = default_context();
+  if (cx) sm = cx->sm_count;
+  Plan p;
+  if (make_plan(rq->n, nseg_user, rq->kt, pairs, rq->levels, rq->buckets_per_level, &rq->opt, sm, &p) != AMS_OK)
+    return 0;
+  Bufs b{};
+  return (uint64_t)carve(p, nullptr, &b);
+}
+
+ams_status ams_context_reserve(void* ctx, uint64_t bytes) {
+  Context* cx = ctx_or_default(ctx);
+  if (!cx) return AMS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(cx->mu);
+  return ensure_ws(cx, (size_t)bytes);
+}
+
 uint64_t ams_context_scratch_bytes(void* ctx) {
   Context* cx = ctx_or_default(ctx);
   return cx ? (uint64_t)(cx->ws_bytes + cx->stage_bytes + cx->step_bytes) : 0;
@@ -798,6 +820,72 @@ ams_status ams_get_stats(void* ctx, ams_stats* out) {
   cx->launches = 0;
   cx->ev_used = 0;
   cx->ev_kind.clear();
+  return AMS_OK;
+}
+
+// ------------------------------------------------------------- level intermediates
+static ams_status level_tables(Context* cx, int level, uint32_t* nseg, const Seg** segs,
+                               const LevelBufs** lb) {
+  if (!cx->has_run) return AMS_ERR_INVALID;
+  const Plan& p = cx->last_plan;
+  if (level < 1 || level > p.L) return AMS_ERR_INVALID;
+  AMS_TRY(cudaStreamSynchronize(cx->last_stream));
+  LevelCounters c;
+  AMS_TRY(cudaMemcpy(&c, &cx->last_bufs.ctr[level], sizeof(c), cudaMemcpyDeviceToHost));
+  *nseg = c.nseg;
+  *segs = level == 1 ? cx->last_bufs.segs1 : cx->last_bufs.lv[level - 2].segs_next;
+  *lb = &cx->last_bufs.lv[level - 1];
+  return AMS_OK;
+}
+
+ams_status ams_get_level_segments(void* ctx, int level, uint32_t* nseg, ams_segment_info* h_segs,
+                                  uint32_t max_seg) {
+  if (!nseg) return AMS_ERR_INVALID;
+  Context* cx = ctx_or_default(ctx);
+  if (!cx) return AMS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(cx->mu);
+  const Seg* segs;
+  const LevelBufs* lb;
+  ams_status st = level_tables(cx, level, nseg, &segs, &lb);
+  if (st != AMS_OK || !h_segs) return st;
+  const uint32_t m = std::min(*nseg, max_seg);
+  if (m == 0) return AMS_OK;
+  std::vector<Seg> sg(m);
+  std::vector<SegInfo> si(m);
+  std::vector<uint32_t> L(m), ng(m), np(m);
+  AMS_TRY(cudaMemcpy(sg.data(), segs, m * sizeof(Seg), cudaMemcpyDeviceToHost));
+  AMS_TRY(cudaMemcpy(si.data(), lb->sinfo, m * sizeof(SegInfo), cudaMemcpyDeviceToHost));
+  AMS_TRY(cudaMemcpy(L.data(), lb->seg_L, m * 4, cudaMemcpyDeviceToHost));
+  AMS_TRY(cudaMemcpy(ng.data(), lb->seg_ng, m * 4, cudaMemcpyDeviceToHost));
+  AMS_TRY(cudaMemcpy(np.data(), lb->npieces, m * 4, cudaMemcpyDeviceToHost));
+  const uint32_t nid = cx->last_plan.lv[level - 1].nid;
+  for (uint32_t i = 0; i < m; ++i)
+    h_segs[i] = ams_segment_info{sg[i].begin, sg[i].end, si[i].a, si[i].S, L[i], ng[i], np[i], nid};
+  return AMS_OK;
+}
+
+ams_status ams_get_segment_tables(void* ctx, int level, uint32_t seg, uint32_t* h_bucket_starts,
+                                  uint16_t* h_piece_of, uint32_t* h_piece_starts) {
+  Context* cx = ctx_or_default(ctx);
+  if (!cx) return AMS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(cx->mu);
+  uint32_t nseg;
+  const Seg* segs;
+  const LevelBufs* lb;
+  ams_status st = level_tables(cx, level, &nseg, &segs, &lb);
+  if (st != AMS_OK) return st;
+  if (seg >= nseg) return AMS_ERR_INVALID;
+  const size_t nid = cx->last_plan.lv[level - 1].nid;
+  if (h_bucket_starts)
+    AMS_TRY(cudaMemcpy(h_bucket_starts, lb->totals + seg * nid, nid * 4, cudaMemcpyDeviceToHost));
+  if (h_piece_of)
+    AMS_TRY(cudaMemcpy(h_piece_of, lb->piece_of + seg * nid, nid * 2, cudaMemcpyDeviceToHost));
+  if (h_piece_starts) {
+    uint32_t np = 0;
+    AMS_TRY(cudaMemcpy(&np, lb->npieces + seg, 4, cudaMemcpyDeviceToHost));
+    if (np > nid) return AMS_ERR_INTERNAL;
+    if (np) AMS_TRY(cudaMemcpy(h_piece_starts, lb->piece_start + seg * nid, np * 4, cudaMemcpyDeviceToHost));
+  }
   return AMS_OK;
 }
 

@@ -87,11 +87,21 @@ struct ams_server {
 
 namespace {
 
-// Scratch a request will hold while in flight: the context's ping-pong copy, the
-// bucket ids and tables (about n * (w + 2) + payloads), plus its staging share.
+// Scratch a request holds while in flight: its context workspace (the library's own
+// figure for the request's plan) plus, for a packable request, its share of the
+// packing stage.
 uint64_t scratch_of(const ams_request& rq) {
-  const uint64_t w = key_bytes(rq.kt) + (rq.vals_in ? 8 : 0);
-  return rq.n * (w + 2) + rq.n * w / 2 + (1u << 20);
+  const uint64_t ws = ams_request_scratch_bytes(&rq);
+  return ws + rq.n * key_bytes(rq.kt) + (1u << 16);
+}
+
+constexpr uint64_t kFreeSpare = 256ull << 20;  // device memory kept free at admission
+
+// Bytes the worker's context would have to add to run `j` (0 if it fits already).
+uint64_t growth_of(const Worker& wk, const Job& j) {
+  const uint64_t need = ams_request_scratch_bytes(&j.rq);
+  const uint64_t have = ams_context_scratch_bytes(wk.ctx);
+  return need > have ? need - have : 0;
 }
 
 ams_status grow_stage(Worker& wk, size_t bytes, size_t segs) {
@@ -197,7 +207,14 @@ void run_loop(ams_server* s) {
     for (Worker& wk : s->workers) {
       if (wk.busy || s->queue.empty()) continue;
       const Job& head = s->queue.front();
-      if (s->in_flight_bytes > 0 && s->in_flight_bytes + head.scratch > s->budget) break;
+      {
+        // admission by budget and by free device memory: a context that must grow
+        // allocates, so the growth has to fit in what the device has free now
+        const uint64_t grow = s->in_flight_bytes > 0 ? growth_of(wk, head) : 0;
+        size_t free_b = 0, total_b = 0;
+        if (grow > 0 && cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) break;
+        if (!ams_server_admits(s->in_flight_bytes, head.scratch, s->budget, grow, free_b)) break;
+      }
       wk.jobs.clear();
       wk.jobs.push_back(head);
       s->in_flight_bytes += head.scratch;
@@ -207,7 +224,7 @@ void run_loop(ams_server* s) {
         while (!s->queue.empty()) {
           const Job& nx = s->queue.front();
           if (!packable(s, nx) || nx.rq.kt != wk.jobs[0].rq.kt || total + nx.rq.n > s->pack_total ||
-              s->in_flight_bytes + nx.scratch > s->budget)
+              (s->budget && s->in_flight_bytes + nx.scratch > s->budget))
             break;
           total += nx.rq.n;
           s->in_flight_bytes += nx.scratch;
@@ -247,7 +264,7 @@ AMS_API ams_status ams_server_create(uint64_t hbm_budget_bytes, int streams, uin
   if (!out || streams < 1 || streams > 64) return AMS_ERR_INVALID;
   *out = nullptr;
   ams_server* s = new ams_server();
-  s->budget = hbm_budget_bytes ? hbm_budget_bytes : ~0ull;
+  s->budget = hbm_budget_bytes;
   s->pack_max = pack_max_keys;
   s->pack_total = pack_max_keys ? pack_max_keys * 64 : 0;
   if (cudaGetDevice(&s->device) != cudaSuccess) {
@@ -270,6 +287,31 @@ AMS_API ams_status ams_server_create(uint64_t hbm_budget_bytes, int streams, uin
   }
   s->loop = std::thread(run_loop, s);
   *out = s;
+  return AMS_OK;
+}
+
+AMS_API int ams_server_admits(uint64_t in_flight, uint64_t scratch, uint64_t budget, uint64_t growth,
+                              uint64_t free_bytes) {
+  if (in_flight == 0) return 1;  // a request larger than everything runs alone
+  if (budget && in_flight + scratch > budget) return 0;
+  if (growth && free_bytes < growth + kFreeSpare) return 0;
+  return 1;
+}
+
+AMS_API ams_status ams_server_reserve(ams_server* s, const ams_request* largest) {
+  if (!s || !largest) return AMS_ERR_INVALID;
+  const uint64_t need = ams_request_scratch_bytes(largest);
+  if (need == 0) return AMS_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);  // (the loop launches only with the lock released)
+  if (cudaSetDevice(s->device) != cudaSuccess) return AMS_ERR_CUDA;
+  for (Worker& wk : s->workers) {
+    if (wk.busy) return AMS_ERR_INVALID;  // reserve before submitting
+    ams_status st = ams_context_reserve(wk.ctx, need);
+    if (st != AMS_OK) return st;
+    // the packing stage holds up to pack_total keys of any type, from at most
+    // pack_total / 1024 requests of 2^10 keys or more (more grow it in the loop)
+    if (s->pack_total && (st = grow_stage(wk, (size_t)s->pack_total * 8, 4096)) != AMS_OK) return st;
+  }
   return AMS_OK;
 }
 

@@ -145,22 +145,33 @@ __device__ void bitonic_block(K* dst, uint64_t* vdst, uint32_t b, uint32_t m, in
 // [lo, hi] for 64-bit keys comes from the high 32-bit words alone (lo = min << 32,
 // hi = max << 32 | 2^32-1) when those span at least 2^12 values -- the range is then
 // overstated by less than 0.1% -- and from the full keys otherwise.
+// Keys [b, b+m) of src into registers: element e = threadIdx.x + q*NT goes to x[q].
 template <typename K, bool PAIRS>
-__device__ __forceinline__ void sort_block(const K* src, K* dst, const uint64_t* vsrc, uint64_t* vdst,
-                                           uint32_t b, uint32_t m, int tf_in, int tf_out,
-                                           const BaseSmem<K>& sm) {
+__device__ __forceinline__ void load_item(const K* src, uint32_t b, uint32_t m, int tf_in,
+                                          K (&x)[BaseCfg<K, PAIRS>::KPT]) {
+  using C = BaseCfg<K, PAIRS>;
+#pragma unroll
+  for (int q = 0; q < C::KPT; ++q) {
+    if ((uint32_t)q * C::NT >= m) break;  // (uniform) the rest of the slots are empty
+    const uint32_t e = threadIdx.x + q * C::NT;
+    x[q] = e < m ? order_in<K>(src[b + e], tf_in) : K(0);
+  }
+}
+
+// Sorts the item whose keys are already in x (load_item) and writes it to dst[b, b+m);
+// payloads are read from vsrc here.  next() is called once the keys in x are no
+// longer needed (it may load the block's next item into x, whose load latency then
+// overlaps this item's ranking); src and dst may be the same buffer, and the next
+// item never overlaps this one.
+template <typename K, bool PAIRS, typename Next>
+__device__ __forceinline__ void sort_loaded(K (&x)[BaseCfg<K, PAIRS>::KPT], K* dst, const uint64_t* vsrc,
+                                            uint64_t* vdst, uint32_t b, uint32_t m, int tf_out,
+                                            const BaseSmem<K>& sm, Next next) {
   using C = BaseCfg<K, PAIRS>;
   constexpr int NT = C::NT, KPT = C::KPT, NW = NT / 32;
   const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  K x[KPT];
-#pragma unroll
-  for (int q = 0; q < KPT; ++q) {
-    if ((uint32_t)q * NT >= m) break;  // (uniform) the rest of the slots are empty
-    const uint32_t e = tid + q * NT;
-    x[q] = e < m ? order_in<K>(src[b + e], tf_in) : K(0);
-    if constexpr (PAIRS) {
-      if (e < m) sm.vals[e] = vsrc[b + e];
-    }
+  if constexpr (PAIRS) {
+    for (uint32_t e = tid; e < m; e += NT) sm.vals[e] = vsrc[b + e];
   }
   // min / max of the keys (32-bit keys) or of their high words (64-bit keys)
   uint32_t* red32 = (uint32_t*)sm.red;  // [0, NW): minima, [NW, 2NW): maxima
@@ -235,6 +246,7 @@ __device__ __forceinline__ void sort_block(const K* src, K* dst, const uint64_t*
         if constexpr (PAIRS) vdst[b + e] = sm.vals[e];
       }
     }
+    next();
     return;
   }
   // cells: M = 2m rounded up to 8 (whole 128-bit words of counters), at most CELLS
@@ -261,51 +273,43 @@ __device__ __forceinline__ void sort_block(const K* src, K* dst, const uint64_t*
     }
   }
   __syncthreads();
-  // exclusive scan of the M 16-bit counters.  Warp w owns the 128-bit words
-  // [w*pv, (w+1)*pv); lane l reads word 32i + l of them (consecutive lanes,
-  // consecutive banks).  (v * 0x10001) >> 16 adds the two counters of a 32-bit word
-  // (their sum is <= CAP: no carry).
+  // exclusive scan of the M 16-bit counters in one pass: thread t owns the 128-bit
+  // words [t*k, (t+1)*k), k = ceil(M/8 / NT) <= 4, sums them, takes its offset from
+  // one block scan and writes the cell starts back.  (v * 0x10001) >> 16 adds the
+  // two counters of a 32-bit word (their sum is <= CAP: no carry).
   uint16_t* c16 = (uint16_t*)sm.cw;
   {
+    static_assert(C::CELLS / 8 <= 4 * NT, "at most four counter words per thread");
     uint32_t* ws = red32 + 2 * NW;  // (bounds above already read by every thread)
     auto sum4 = [](const uint4& v) {
       return ((v.x * 0x10001u) >> 16) + ((v.y * 0x10001u) >> 16) + ((v.z * 0x10001u) >> 16) +
              ((v.w * 0x10001u) >> 16);
     };
-    const uint32_t pv = (nv + NW - 1) / NW;
-    const uint32_t vb = min(w * pv, nv), ve = min(vb + pv, nv);
+    const uint32_t k = (nv + NT - 1) / NT;
+    const uint32_t vb = min(tid * k, nv), ve = min(vb + k, nv);
     uint4* cv = (uint4*)sm.cw;
-    uint32_t s = 0;
-    for (uint32_t i = vb + lane; i < ve; i += 32) s += sum4(cv[i]);
-    s = __reduce_add_sync(0xFFFFFFFFu, s);
-    if (lane == 0) ws[w] = s;
-    __syncthreads();
-    uint32_t carry = __reduce_add_sync(0xFFFFFFFFu, lane < w ? ws[lane] : 0u);  // warps before w
-    for (uint32_t i0 = vb; i0 < ve; i0 += 32) {  // (warp-uniform trip count)
-      const uint32_t i = i0 + lane;
-      uint4 v = i < ve ? cv[i] : make_uint4(0, 0, 0, 0);
-      const uint32_t t = sum4(v);
-      uint32_t inc = t;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-        if (lane >= (uint32_t)o) inc += y;
-      }
-      // largest counter of the word group (16-bit lane-wise maxima)
-      const uint32_t mx = __vmaxu2(__vmaxu2(v.x, v.y), __vmaxu2(v.z, v.w));
-      if (max(mx & 0xFFFFu, mx >> 16) > C::BIGCELL) sm.flag[0] = 1;
-      uint32_t run = carry + inc - t;
-      auto pre = [&](uint32_t u) {  // word (lo, hi) -> (run, run + lo)
-        const uint32_t o = run * 0x10001u + (u << 16);
-        run += (u * 0x10001u) >> 16;
-        return o;
-      };
-      v.x = pre(v.x);
-      v.y = pre(v.y);
-      v.z = pre(v.z);
-      v.w = pre(v.w);
-      if (i < ve) cv[i] = v;
-      carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
+    uint32_t t = 0, mx = 0;
+    for (uint32_t i = vb; i < ve; ++i) {
+      const uint4 v = cv[i];
+      t += sum4(v);
+      // largest counter (16-bit lane-wise maxima)
+      mx = __vmaxu2(mx, __vmaxu2(__vmaxu2(v.x, v.y), __vmaxu2(v.z, v.w)));
+    }
+    if (max(mx & 0xFFFFu, mx >> 16) > C::BIGCELL) sm.flag[0] = 1;
+    uint32_t total;
+    uint32_t run = block_exclusive_scan<NT, uint32_t>(t, ws, total);  // (barriers)
+    auto pre = [&](uint32_t u) {  // word (lo, hi) -> (run, run + lo)
+      const uint32_t o = run * 0x10001u + (u << 16);
+      run += (u * 0x10001u) >> 16;
+      return o;
+    };
+    for (uint32_t i = vb; i < ve; ++i) {  // (re-read: the words are not kept in registers)
+      uint4 u = cv[i];
+      u.x = pre(u.x);
+      u.y = pre(u.y);
+      u.z = pre(u.z);
+      u.w = pre(u.w);
+      cv[i] = u;
     }
   }
   __syncthreads();
@@ -319,6 +323,7 @@ __device__ __forceinline__ void sort_block(const K* src, K* dst, const uint64_t*
       if constexpr (PAIRS) sm.pos[s] = (uint16_t)e;
     }
   }
+  next();  // the keys are in shared memory now
   __syncthreads();
   // Cells above BIGCELL keys come from repeated values (equal keys share a cell): if
   // the item has such cells, mark those holding more than one value; the others are
@@ -350,6 +355,11 @@ __device__ __forceinline__ void sort_block(const K* src, K* dst, const uint64_t*
       const K v = sm.keys[s];
       const uint32_t c = cell(v);
       const uint32_t cb = c ? c16[c - 1] : 0u, ce = c16[c];
+      if (ce - cb == 1) {  // alone in its cell: its place is the cell start
+        dst[b + cb] = order_out<K>(v, tf_out);
+        if constexpr (PAIRS) vdst[b + cb] = sm.vals[sm.pos[s]];
+        continue;
+      }
       const bool one_value = one_value_check(c, ce - cb);
       uint32_t r = 0;
       if constexpr (PAIRS) {
@@ -388,6 +398,16 @@ __device__ __forceinline__ void sort_block(const K* src, K* dst, const uint64_t*
   } else {
     rank_all([](uint32_t, uint32_t) { return false; });
   }
+}
+
+// One item on its own (no prefetch).
+template <typename K, bool PAIRS>
+__device__ __forceinline__ void sort_block(const K* src, K* dst, const uint64_t* vsrc, uint64_t* vdst,
+                                           uint32_t b, uint32_t m, int tf_in, int tf_out,
+                                           const BaseSmem<K>& sm) {
+  K x[BaseCfg<K, PAIRS>::KPT];
+  load_item<K, PAIRS>(src, b, m, tf_in, x);
+  sort_loaded<K, PAIRS>(x, dst, vsrc, vdst, b, m, tf_out, sm, [] {});
 }
 
 template <typename K, bool PAIRS>
@@ -448,18 +468,32 @@ __global__ void __launch_bounds__(512, BaseCfg<K, PAIRS>::MINB) k_basecase(BaseA
   const uint32_t nitems = *a.nitems;
   const K* src = (const K*)a.src;
   K* out = (K*)a.out;
+  // the keys of the block's next sort item are loaded into x while the current item
+  // is ranked (see sort_loaded)
+  auto sortable = [&](const BcItem& it) { return it.kind == BC_SORT && it.end - it.begin <= C::CAP; };
+  const BcItem none{0, 0, BC_COPY, 0};
+  BcItem item = blockIdx.x < nitems ? a.items[blockIdx.x] : none;
+  K x[C::KPT];
+  if (sortable(item)) load_item<K, PAIRS>(src, item.begin, item.end - item.begin, a.tf_load, x);
   for (uint32_t it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const BcItem item = a.items[it];
+    const BcItem nxt = it + gridDim.x < nitems ? a.items[it + gridDim.x] : none;
+    auto prefetch = [&] {
+      if (sortable(nxt)) load_item<K, PAIRS>(src, nxt.begin, nxt.end - nxt.begin, a.tf_load, x);
+    };
     const uint32_t b = item.begin, m = item.end - item.begin;
     if (item.kind == BC_COPY) {
       for (uint32_t e = threadIdx.x; e < m; e += C::NT) {
         out[b + e] = order_out<K>(order_in<K>(src[b + e], a.tf_load), a.tf_store);
         if constexpr (PAIRS) a.vout[b + e] = a.vsrc[b + e];
       }
+      prefetch();
     } else if (m <= C::CAP) {
-      sort_block<K, PAIRS>(src, out, a.vsrc, a.vout, b, m, a.tf_load, a.tf_store, sm);
+      sort_loaded<K, PAIRS>(x, out, a.vsrc, a.vout, b, m, a.tf_store, sm, prefetch);
+    } else {
+      prefetch();
     }
     __syncthreads();
+    item = nxt;
   }
 }
 

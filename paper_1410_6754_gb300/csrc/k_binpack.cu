@@ -16,6 +16,8 @@
 //     the rest of the group stays one piece; pieces larger than C go to the next
 //     level (or to the global-memory fallback on the last level), smaller ones are
 //     packed into base-case items of at most C keys.
+#include <type_traits>
+
 #include "cta_utils.cuh"
 
 namespace ams {
@@ -74,22 +76,51 @@ __device__ ScanResult warp_scan_groups(const uint32_t* P, uint32_t B, uint32_t r
   return res;
 }
 
+// What the pieces of a group produce: base-case items (with their keys), next-level
+// segments, and groups above capacity on the last level.  Emission runs twice per
+// block: once counting (Counter), then -- after a block scan of the counts and one
+// global atomic per counter and block -- writing at the reserved indices (Writer), so
+// that the many items of a level do not contend on one global counter.
+struct EmitCounts {
+  uint32_t bc, bc_keys, next, big;
+};
+
+struct Counter {
+  EmitCounts c{0, 0, 0, 0};
+  __device__ void bc(uint32_t b, uint32_t e, uint32_t) { ++c.bc; c.bc_keys += e - b; }
+  __device__ void next(uint32_t, uint32_t) { ++c.next; }
+  __device__ void big(uint32_t, uint32_t) { ++c.big; }
+};
+
+struct Writer {
+  const LevelArgs* a;
+  EmitCounts at;  // next free index of each table (reserved for this thread)
+  __device__ void bc(uint32_t b, uint32_t e, uint32_t kind) {
+    const uint32_t i = at.bc++;
+    if (i < a->bc_cap) a->bc[i] = BcItem{b, e, kind, 0};
+    else atomicOr(a->status, ST_OVERFLOW);
+  }
+  __device__ void next(uint32_t b, uint32_t e) {
+    const uint32_t i = at.next++;
+    if (i < a->next_cap) a->segs_next[i] = Seg{b, e};
+    else atomicOr(a->status, ST_OVERFLOW);
+  }
+  __device__ void big(uint32_t b, uint32_t e) {
+    const uint32_t i = at.big++;
+    if (i < a->big_cap) a->big[i] = BcItem{b, e, BC_BIG, 0};
+    else atomicOr(a->status, ST_OVERFLOW);
+  }
+};
+
+template <typename Sink>
 struct Emitter {
   const LevelArgs* a;
+  Sink* sink;
   uint32_t seg_begin;
   uint32_t cur_b, cur_e;  // open base-case item (relative positions), empty if equal
 
-  __device__ void push_bc(uint32_t b, uint32_t e, uint32_t kind) {
-    const uint32_t i = atomicAdd(&a->ctr->n_bc, 1u);
-    atomicAdd(&a->ctr->bc_keys, e - b);
-    if (i < a->bc_cap) {
-      a->bc[i] = BcItem{seg_begin + b, seg_begin + e, kind, 0};
-    } else {
-      atomicOr(a->status, ST_OVERFLOW);
-    }
-  }
   __device__ void flush() {
-    if (cur_e > cur_b) push_bc(cur_b, cur_e, BC_SORT);
+    if (cur_e > cur_b) sink->bc(seg_begin + cur_b, seg_begin + cur_e, BC_SORT);
     cur_b = cur_e = 0;
   }
   __device__ void leaf(uint32_t b, uint32_t e) {
@@ -111,24 +142,12 @@ struct Emitter {
     flush();
     if (fin) {
       if (a->copy_final)
-        for (uint32_t c = b; c < e; c += kCopyChunk) push_bc(c, min(e, c + kCopyChunk), BC_COPY);
+        for (uint32_t c = b; c < e; c += kCopyChunk)
+          sink->bc(seg_begin + c, seg_begin + min(e, c + kCopyChunk), BC_COPY);
       return;
     }
-    if (!a->last) {
-      const uint32_t i = atomicAdd(&a->ctr->nseg_next, 1u);
-      if (i < a->next_cap) {
-        a->segs_next[i] = Seg{seg_begin + b, seg_begin + e};
-      } else {
-        atomicOr(a->status, ST_OVERFLOW);
-      }
-    } else {
-      const uint32_t i = atomicAdd(&a->ctr->n_big, 1u);
-      if (i < a->big_cap) {
-        a->big[i] = BcItem{seg_begin + b, seg_begin + e, BC_BIG, 0};
-      } else {
-        atomicOr(a->status, ST_OVERFLOW);
-      }
-    }
+    if (!a->last) sink->next(seg_begin + b, seg_begin + e);
+    else sink->big(seg_begin + b, seg_begin + e);
   }
 };
 
@@ -144,6 +163,7 @@ __global__ void __launch_bounds__(512, 2) k_binpack(LevelArgs a) {
   __shared__ unsigned long long lohi[2];
   __shared__ ScanResult wres[32];
   __shared__ uint32_t ngroups_s, best_s;
+  __shared__ uint32_t base_s[3];
   __shared__ int best_w;
   const uint32_t nseg = a.ctr->nseg;
   const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -284,21 +304,42 @@ __global__ void __launch_bounds__(512, 2) k_binpack(LevelArgs a) {
         }
       }
     }
-    for (uint32_t k = tid; k < ng; k += NT) {
-      Emitter em{&a, sg.begin, 0, 0};
-      const uint32_t gs = k ? ends[k - 1] : 0, ge = ends[k];
-      const uint32_t id_lo = 2 * gs, id_hi = min(2 * ge, nid);
-      uint32_t run = bst_s[id_lo];
-      for (uint32_t i = id_lo | 1; i < id_hi; i += 2) {
-        if (cnt_s[i] >= tau) {
-          em.piece(run, bst_s[i], false);
-          em.piece(bst_s[i], bst_s[i + 1], true);
-          run = bst_s[i + 1];
+    // the pieces of this thread's groups: base-case items, next-level segments, big
+    // groups -- counted, then written at indices reserved with one atomic per table
+    auto emit_groups = [&](auto& sink) {
+      using S = typename std::remove_reference<decltype(sink)>::type;
+      for (uint32_t k = tid; k < ng; k += NT) {
+        Emitter<S> em{&a, &sink, sg.begin, 0, 0};
+        const uint32_t gs = k ? ends[k - 1] : 0, ge = ends[k];
+        const uint32_t id_lo = 2 * gs, id_hi = min(2 * ge, nid);
+        uint32_t run = bst_s[id_lo];
+        for (uint32_t i = id_lo | 1; i < id_hi; i += 2) {
+          if (cnt_s[i] >= tau) {
+            em.piece(run, bst_s[i], false);
+            em.piece(bst_s[i], bst_s[i + 1], true);
+            run = bst_s[i + 1];
+          }
         }
+        em.piece(run, bst_s[id_hi], false);
+        em.flush();
       }
-      em.piece(run, bst_s[id_hi], false);
-      em.flush();
+    };
+    Counter cn;
+    emit_groups(cn);
+    EmitCounts off, all;
+    off.bc = block_exclusive_scan<NT, uint32_t>(cn.c.bc, ws, all.bc);
+    off.bc_keys = block_exclusive_scan<NT, uint32_t>(cn.c.bc_keys, ws, all.bc_keys);
+    off.next = block_exclusive_scan<NT, uint32_t>(cn.c.next, ws, all.next);
+    off.big = block_exclusive_scan<NT, uint32_t>(cn.c.big, ws, all.big);
+    if (tid == 0) {
+      base_s[0] = all.bc ? atomicAdd(&a.ctr->n_bc, all.bc) : 0u;
+      if (all.bc_keys) atomicAdd(&a.ctr->bc_keys, all.bc_keys);
+      base_s[1] = all.next ? atomicAdd(&a.ctr->nseg_next, all.next) : 0u;
+      base_s[2] = all.big ? atomicAdd(&a.ctr->n_big, all.big) : 0u;
     }
+    __syncthreads();
+    Writer wr{&a, EmitCounts{base_s[0] + off.bc, 0, base_s[1] + off.next, base_s[2] + off.big}};
+    emit_groups(wr);
     __syncthreads();
   }
 }

@@ -12,49 +12,60 @@
 namespace ams {
 
 // ---------------------------------------------------------------------------- table
-// Over the D distinct splitter values: J[c] = #{values whose cell is below c} = the
-// first distinct index whose cell is >= c (the cells of the sorted values do not
-// decrease).
+// Over the D distinct splitter values: J[c] = #{values whose cell is below c}.  A
+// histogram of the values' cells (16-bit counters, two per word) and one exclusive
+// block scan over the cells give J; every thread owns 32 consecutive cells and writes
+// J2[c] = J[c] | J[c+1] << 16 for them.  The widest span is the largest counter.
 template <typename K>
 __global__ void __launch_bounds__(512) k_table(LevelArgs a) {
   constexpr int NT = 512;
-  __shared__ uint32_t cs[kMaxBuckets];    // cell of every distinct value
-  __shared__ uint32_t dix[kMaxBuckets];   // distinct index of every splitter
+  constexpr uint32_t PER = kCells / NT;  // cells per thread
+  static_assert(PER % 2 == 0, "whole counter words per thread");
+  __shared__ uint32_t cw[kCells / 2];    // cell counters, 16 bits each
+  __shared__ uint32_t dix[kMaxBuckets];  // distinct index of every splitter
   __shared__ uint32_t ws[NT / 32 + 1];
   const uint32_t nseg = a.ctr->nseg;
   const uint32_t B = a.B, ns = B - 1;
+  const uint32_t tid = threadIdx.x;
   for (uint32_t g = blockIdx.x; g < nseg; g += gridDim.x) {
     const K* spl_g = (const K*)a.spl + (size_t)g * ns;
     const K lo = spl_g[0], hi = spl_g[ns - 1];
     const uint32_t sh = cell_shift<K>(lo, hi);
     auto starts = [&](uint32_t i) { return i == 0 || spl_g[i] != spl_g[i - 1]; };
-    for (uint32_t i = threadIdx.x; i < ns; i += NT) dix[i] = starts(i) ? 1u : 0u;
+    for (uint32_t i = tid; i < kCells / 2; i += NT) cw[i] = 0;
+    for (uint32_t i = tid; i < ns; i += NT) dix[i] = starts(i) ? 1u : 0u;
     __syncthreads();
-    const uint32_t D = block_scan_array<NT, uint32_t>(dix, ns, ws);
-    for (uint32_t i = threadIdx.x; i < ns; i += NT)
-      if (starts(i)) cs[dix[i]] = cell_of<K>(spl_g[i], lo, sh);
-    __syncthreads();
-    auto first_at_least = [&](uint32_t c) {  // #{d : cs[d] < c}
-      uint32_t l = 0, h = D;
-      while (l < h) {
-        const uint32_t m = (l + h) >> 1;
-        if (cs[m] < c) l = m + 1; else h = m;
+    const uint32_t D = block_scan_array<NT, uint32_t>(dix, ns, ws);  // (ends with a barrier)
+    for (uint32_t i = tid; i < ns; i += NT) {
+      if (starts(i)) {
+        const uint32_t c = cell_of<K>(spl_g[i], lo, sh);
+        atomicAdd(&cw[c >> 1], 1u << ((c & 1) << 4));
       }
-      return l;
-    };
-    uint32_t* J2 = a.J2 + (size_t)g * kCells;
-    uint32_t span = 0;
-    for (uint32_t c = threadIdx.x; c < kCells; c += NT) {
-      const uint32_t j0 = first_at_least(c);
-      const uint32_t j1 = c + 1 == kCells ? D : first_at_least(c + 1);
-      J2[c] = j0 | (j1 << 16);
-      span = max(span, j1 - j0);
     }
-    const uint32_t mspan = block_reduce_max<NT, uint32_t>(span, ws);
-    if (threadIdx.x == 0) {
+    __syncthreads();
+    // thread t: cells [t*PER, (t+1)*PER)
+    uint32_t sum = 0, mspan = 0;
+#pragma unroll 4
+    for (uint32_t i = 0; i < PER / 2; ++i) {
+      const uint32_t v = cw[tid * (PER / 2) + i];
+      sum += (v & 0xFFFFu) + (v >> 16);
+      mspan = max(mspan, max(v & 0xFFFFu, v >> 16));
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan<NT, uint32_t>(sum, ws, total);  // J of the first cell
+    uint32_t* J2 = a.J2 + (size_t)g * kCells + tid * PER;
+#pragma unroll 4
+    for (uint32_t i = 0; i < PER / 2; ++i) {
+      const uint32_t v = cw[tid * (PER / 2) + i];
+      const uint32_t j1 = run + (v & 0xFFFFu), j2 = j1 + (v >> 16);
+      *(uint2*)(J2 + 2 * i) = make_uint2(run | (j1 << 16), j1 | (j2 << 16));
+      run = j2;
+    }
+    const uint32_t wide = block_reduce_max<NT, uint32_t>(mspan, ws);
+    if (tid == 0) {
       ClsHead<K> h;
       h.lo = lo;
-      h.sh_steps = sh | ((mspan ? 32u - __clz((int)mspan) : 0u) << 8);
+      h.sh_steps = sh | ((wide ? 32u - __clz((int)wide) : 0u) << 8) | (min(wide, 255u) << 16);
       h.D = D;
       ((ClsHead<K>*)a.cls_head)[g] = h;
     }

@@ -64,6 +64,8 @@ def test_struct_layouts_match_header(tmp_path):
         "ams_stats": (ams.Stats, ["levels_planned", "kernel_launches", "segments", "basecase_items",
                                   "device_status", "kernel_ms", "kernel_calls", "kernel_elems"]),
         "ams_tuned": (ams.Tuned, ["levels", "buckets_per_level", "overpartition_b", "candidates", "ms"]),
+        "ams_segment_info": (ams.SegmentInfo, ["begin", "end", "a", "S", "L", "ngroups", "npieces",
+                                               "nbucket_ids"]),
     }
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "ams.h"', "int main(void) {"]
     for st, (_, names) in fields.items():
@@ -104,3 +106,18 @@ def test_noalloc_refuses_misaligned_views_on_the_host(libpath):
         == ams.ERR_INVALID
     assert L.ams_sort_small_noalloc(p(0x10000), None, 10, 7, None) == ams.ERR_INVALID
     assert L.ams_sort_small_noalloc(None, None, 0, ams.U32, None) == ams.OK
+
+
+def test_server_admission_rule(libpath):
+    """The serving loop's admission decision (a pure function; no GPU): by the budget of
+    scratch in flight, and by the device's free memory when a worker context must grow."""
+    L = ams.lib()
+    GiB, MiB = 1 << 30, 1 << 20
+    adm = L.ams_server_admits
+    assert adm(0, 100 * GiB, 64 * GiB, 50 * GiB, 0) == 1          # nothing in flight: runs alone
+    assert adm(10 * GiB, 50 * GiB, 64 * GiB, 0, 0) == 1           # within budget, no growth
+    assert adm(10 * GiB, 55 * GiB, 64 * GiB, 0, 0) == 0           # over budget
+    assert adm(10 * GiB, 55 * GiB, 0, 0, 0) == 1                  # no budget set
+    assert adm(10 * GiB, 1 * GiB, 64 * GiB, 1 * GiB, 2 * GiB) == 1  # growth fits in free memory
+    assert adm(10 * GiB, 1 * GiB, 64 * GiB, 1 * GiB, 1 * GiB + 255 * MiB) == 0  # not with the spare
+    assert adm(10 * GiB, 1 * GiB, 64 * GiB, 1 * GiB, 1 * GiB + 256 * MiB) == 1

@@ -85,6 +85,33 @@ def test_classify(kt, bits, B):
     assert np.array_equal(to_np(counts, np.uint32).astype(np.int64), O.bucket_counts(exp_ids, B))
 
 
+@pytest.mark.parametrize("kt,bits", KTS)
+@pytest.mark.parametrize("B", [2, 3, 17, 256, 1024, 2048])
+def test_classify_uniform_short_spans(kt, bits, B):
+    """Distinct, evenly spread splitters (the short-span path of the table classifier:
+    at most three splitter values per cell), keys equal to splitters, keys below the
+    first splitter, and keys equal to the largest key above every splitter."""
+    dt = ordered_dtype(kt)
+    n = 200003
+    keys = _keys(kt, bits, "uniform", n, 1000 + B)
+    t = O.ordered_keys(kt, keys)
+    spl = np.unique(np.sort(t[np.random.default_rng(B).integers(0, n, size=B - 1)]))
+    while len(spl) < B - 1:  # (distinct splitters)
+        spl = np.unique(np.concatenate([spl, spl[-1:] + np.arange(1, B, dtype=np.uint64)]))[:B - 1]
+    spl = spl.astype(np.uint64)
+    if kt != O.KT_F32:
+        keys = keys.copy()
+        keys[:7] = np.iinfo(dt).max                       # above every splitter
+        keys[7:14] = spl[np.arange(7) % len(spl)].astype(dt)  # equal to splitters
+        keys[14:21] = 0
+        t = O.ordered_keys(kt, keys)
+    counts, ids = ams.step_classify(to_dev(keys), to_dev(spl.astype(dt)), B, kt=kt)
+    torch.cuda.synchronize()
+    exp_ids = O.classify(spl, B, t)
+    assert np.array_equal(to_np(ids, np.uint16).astype(np.int64), exp_ids)
+    assert np.array_equal(to_np(counts, np.uint32).astype(np.int64), O.bucket_counts(exp_ids, B))
+
+
 def _golden_binpack():
     import os
     path = os.path.join(os.path.dirname(__file__), "golden", "binpack_examples.txt")
