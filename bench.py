@@ -424,7 +424,8 @@ def serving_bench(n_requests, streams, tuned, seed=5):
     for kt, src, _, _ in req:
         if tuned:
             cfg = ams.tune(src.numel(), kt)
-            plans.append(dict(levels=cfg["levels"], buckets=cfg["buckets"], b=cfg["b"]))
+            plans.append(dict(levels=cfg["levels"], buckets=cfg["buckets"], b=cfg["b"], a=cfg["a"],
+                              cap=cfg["cap"]))
         else:
             plans.append(dict(levels=2, buckets=[64, 64]))
     t_tune = time.perf_counter() - t_tune

@@ -275,20 +275,52 @@ AMS_API ams_status ams_step_partition(const void* d_in, void* d_out, const uint6
 AMS_API ams_status ams_step_base_case(void* d_keys, uint64_t* d_vals, uint64_t n, ams_key_type kt,
                               void* stream);
 
+/* --------------------------------------------------------------- RLM-sort
+ * Section 5 ("recurse last" multilevel multiway mergesort), the paper's other
+ * algorithm, with perfect load balance.  Tiles of `run` consecutive positions play
+ * the processing elements.  Level 0: every tile is sorted locally.  Level l (l = 1 ..
+ * levels): every part of the previous level (level 0: the whole input) is split into
+ * parts_per_level[l-1] parts whose sizes differ by at most one (part j of a part of m
+ * elements starts floor(j m / r) after it) by multisequence selection over the part's
+ * tiles (Section 4.1: quickselect on sorted sequences, pivots drawn from a SplitMix64
+ * stream of (seed, level, part, rank)); every part receives its pieces in tile order
+ * (data delivery); then every tile of the new part merges the pieces it holds (the
+ * local merge, done by the shared-memory sort: the pieces are sorted, so the result is
+ * their merge), which gives the sorted sequences of the next level.  The result
+ * (d_keys_out, and d_vals_out when d_vals_in is not NULL) is the same as
+ * ams_sort_keys_into / ams_sort_pairs_into give; d_keys_out may equal d_keys_in.
+ *  - run in [2, base-case capacity] (ams_default_basecase_cap); the parts of the last
+ *    level must not exceed `run` (choose the product of the part counts >= n / run);
+ *    otherwise AMS_ERR_UNSUPPORTED.  levels in [0, 8]; 0 sorts tiles only (n <= run).
+ *  - Scratch: n keys (and payloads) plus the part, tile and cut tables, in ctx (NULL =
+ *    default context); asynchronous on `stream`; device errors are latched in the
+ *    context (ams_context_sync). */
+AMS_API ams_status ams_rlm_sort(void* ctx, const void* d_keys_in, void* d_keys_out,
+                                const uint64_t* d_vals_in, uint64_t* d_vals_out, uint64_t n,
+                                ams_key_type kt, uint32_t run, int levels,
+                                const uint32_t* parts_per_level, uint64_t seed, void* stream);
+
 /* --------------------------------------------------------------- autotuner
- * Picks the plan of a size class: for (key type, pairs, ceil(log2 n)) it times a few
- * candidate plans -- 1, 2 or 3 distribution levels, groups per level r a power of two
- * near (n / t)^(1/levels) for target leaf sizes t = C/2 and C/4, b = 1 for one level
- * and 4 otherwise (Section 7 tunes a and b the same way, by measurement) -- on n
- * synthetic uniform keys in ctx's scratch (ctx NULL = default context), and keeps the
- * fastest in a table shared by the process (later calls for the class return it at
- * once).  Allocates and frees 2n keys (and payloads) of device memory per tuning. */
+ * Picks the plan of a size class by measurement (Section 7 tunes a and b the same
+ * way): for (key type, pairs, ceil(log2 n)) it times candidate plans on n synthetic
+ * uniform keys and on n duplicate-heavy keys (P(rank k) ~ 1/k over 2^20 values) in
+ * ctx's scratch (ctx NULL = default context), scoring a plan by the sum of its two
+ * times.  Round 1 picks the shape: 1, 2 or 3 distribution levels, groups per level r
+ * a power of two near (n / t)^(1/levels) for target leaf sizes t = C/2 and C/4, at
+ * the default a and b.  Round 2 tries, on that shape, b = 16 with the default a
+ * (Section 7.2's b = 16, a = 1.6 log10 n), a = 1 with b = 64 (the appendix's sweep),
+ * a = 1 with the default b, a = 1 with b = 16 (each while b * r <= 2048) and half the
+ * base-case capacity C.  The fastest plan is kept in a table shared by the process
+ * (later calls for the class return it at once).  Allocates and frees 3n keys (and
+ * 2n payloads) of device memory per tuning. */
 typedef struct ams_tuned {
   int levels;
   uint32_t buckets_per_level[8];  /* r per level, `levels` entries */
-  uint32_t overpartition_b;
+  uint32_t overpartition_b;       /* b */
   uint32_t candidates;            /* plans timed */
-  float ms;                       /* time of the chosen plan on the synthetic keys */
+  float ms;                       /* score of the chosen plan (sum of the two times) */
+  uint32_t oversample_a;          /* a; 0 = the per-segment rule */
+  uint32_t basecase_cap;          /* C; 0 = the default capacity */
 } ams_tuned;
 AMS_API ams_status ams_tune(void* ctx, uint64_t n, ams_key_type kt, int pairs, void* stream, ams_tuned* out);
 

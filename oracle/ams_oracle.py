@@ -23,6 +23,7 @@ __all__ = [
     "rank_sort", "rank_sort_literal", "splitters", "classify", "classify_literal",
     "bucket_counts", "greedy_groups", "bin_pack", "eq_cut_threshold", "pieces",
     "stable_partition", "piece_of_ids", "Plan", "plan", "ams_sort", "default_basecase_cap",
+    "multiseq_select_definition", "multiseq_select", "rlm_sort",
 ]
 
 KT_U32, KT_U64, KT_F32 = 0, 1, 2
@@ -517,3 +518,137 @@ def ams_sort(kt: int, keys: np.ndarray, pl: Plan, seed: int, vals=None, offsets=
     if vals is None:
         return out_k
     return out_k, np.asarray(vals)[src_idx]
+
+
+# --------------------------------------------------------------------------------------
+# RLM-sort (Section 5, "recurse last" multilevel multiway mergesort) and its building
+# block, multisequence selection (Section 4.1).
+#
+# Sequences are sorted arrays of ordered keys (uint64); the total order among all
+# their elements is (key, sequence index, position in the sequence), the tie breaking
+# of Section 2 / Appendix D when the sequences hold consecutive input ranges in input
+# order (then it is (key, original index)).
+# --------------------------------------------------------------------------------------
+
+def multiseq_select_definition(seqs, k: int):
+    """The split positions (s_1, ..., s_p) of rank k: the first k elements of the total
+    order are exactly the prefixes seqs[i][:s_i].  numpy's lexsort over (key, sequence,
+    position) is the library step."""
+    keys = np.concatenate([np.asarray(q, dtype=np.uint64) for q in seqs]) if seqs else np.zeros(0, np.uint64)
+    sid = np.concatenate([np.full(len(q), i, dtype=np.int64) for i, q in enumerate(seqs)]) if seqs else \
+        np.zeros(0, np.int64)
+    order = np.lexsort((np.arange(len(keys)), keys))  # ties: concatenation order = (sequence, position)
+    first = sid[order[:k]]
+    return [int(np.sum(first == i)) for i in range(len(seqs))]
+
+
+def _count_before(q, key, i, pivot_seq, pivot_pos):
+    """Elements of sorted sequence q (index i) that precede the pivot element
+    (key, pivot_seq, pivot_pos) in the total order."""
+    if i < pivot_seq:
+        return int(np.searchsorted(q, key, side="right"))
+    if i > pivot_seq:
+        return int(np.searchsorted(q, key, side="left"))
+    return pivot_pos
+
+
+def multiseq_select(seqs, k: int, seed: int = 0):
+    """Section 4.1: quickselect on sorted sequences.  Windows [lo_i, hi_i) hold the split
+    position of every sequence; a pivot drawn uniformly from the windows' elements
+    (SplitMix64 stream from `seed`) is located in every sequence by binary search;
+    if fewer than k elements precede it the pivot and everything before it are taken
+    (lo moves up), otherwise the windows end at the pivot (hi moves down).  Returns the
+    same positions as the definition (they are unique)."""
+    seqs = [np.asarray(q, dtype=np.uint64) for q in seqs]
+    p = len(seqs)
+    lo = [0] * p
+    hi = [len(q) for q in seqs]
+    state = mix64((seed * _GAMMA + k) & _M64)
+    while sum(lo) < k:
+        sizes = [hi[i] - lo[i] for i in range(p)]
+        total = sum(sizes)
+        state = (state + _GAMMA) & _M64
+        u = (mix64(state) * total) >> 64          # uniform index among the window elements
+        ps = 0
+        while u >= sizes[ps]:
+            u -= sizes[ps]
+            ps += 1
+        pp = lo[ps] + u                             # pivot: element (seqs[ps][pp], ps, pp)
+        key = seqs[ps][pp]
+        before = [min(max(_count_before(seqs[i], key, i, ps, pp), lo[i]), hi[i]) for i in range(p)]
+        a = sum(before)
+        if a < k:                                   # pivot and all before it are in the first k
+            lo = before
+            lo[ps] = pp + 1
+        else:                                       # the first k all precede the pivot
+            hi = before
+    return lo
+
+
+def rlm_sort(kt: int, keys: np.ndarray, run: int, parts, vals=None, trace=None):
+    """Section 5, RLM-sort ("recurse last") on one device, with a processing element's
+    data played by a tile of `run` consecutive positions.  Level 0: every tile sorts
+    its elements locally (stable: (key, original index)).  Level l = 1..len(parts):
+    every current part is split into parts[l-1] parts of equal size (sizes
+    floor(j m / r) apart) by multisequence selection over the part's tiles; part j
+    receives from every tile the piece between its split positions, in tile order
+    (data delivery); then every tile of the new part -- `run` consecutive positions
+    from the part's start -- merges the pieces it holds locally (here a stable sort
+    of the tile, the library step; the pieces are sorted, so this is their multiway
+    merge), and those tiles are the sorted sequences the next level splits.  A part
+    still larger than one tile after the last level is merged as a whole.  Returns
+    the sorted keys (and values); `trace` gets, per level and part, its range, the
+    split ranks and the split positions in each of its tiles."""
+    keys = np.asarray(keys)
+    n = len(keys)
+    t = ordered_keys(kt, keys)
+    idx = np.arange(n, dtype=np.int64)
+
+    def merge_tiles(lo, hi):
+        tiles = []
+        for b in range(lo, hi, run):
+            e = min(hi, b + run)
+            perm = np.argsort(t[b:e], kind="stable")
+            t[b:e] = t[b:e][perm]
+            idx[b:e] = idx[b:e][perm]
+            tiles.append((b, e))
+        return tiles
+
+    cur = [(0, n, merge_tiles(0, n))] if n else []
+    for level, r in enumerate(parts, start=1):
+        nxt = []
+        for (lo, hi, sq) in cur:
+            m = hi - lo
+            ranks = [(j * m) // r for j in range(r + 1)]
+            arrays = [t[b:e] for (b, e) in sq]
+            cuts = [[0] * len(sq)] + [multiseq_select_definition(arrays, k) for k in ranks[1:-1]] + \
+                   [[e - b for (b, e) in sq]]
+            new_t = t[lo:hi].copy()
+            new_i = idx[lo:hi].copy()
+            pos = 0
+            for j in range(r):
+                for si, (b, e) in enumerate(sq):
+                    pb, pe = b + cuts[j][si], b + cuts[j + 1][si]
+                    new_t[pos:pos + pe - pb] = t[pb:pe]
+                    new_i[pos:pos + pe - pb] = idx[pb:pe]
+                    pos += pe - pb
+            assert pos == m
+            t[lo:hi] = new_t
+            idx[lo:hi] = new_i
+            if trace is not None:
+                trace.append(dict(level=level, begin=lo, end=hi, ranks=ranks, cuts=cuts, tiles=list(sq)))
+            for j in range(r):
+                pb, pe = lo + ranks[j], lo + ranks[j + 1]
+                nxt.append((pb, pe, merge_tiles(pb, pe)))
+        cur = nxt
+    for (lo, hi, sq) in cur:                          # a part of several tiles: merge it whole
+        if len(sq) > 1:
+            perm = np.argsort(t[lo:hi], kind="stable")
+            t[lo:hi] = t[lo:hi][perm]
+            idx[lo:hi] = idx[lo:hi][perm]
+    out_k = unordered_keys(kt, t)
+    if kt != KT_F32:
+        out_k = out_k.astype(keys.dtype)
+    if vals is None:
+        return out_k
+    return out_k, np.asarray(vals)[idx]

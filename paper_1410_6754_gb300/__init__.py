@@ -60,7 +60,7 @@ class SegmentInfo(ctypes.Structure):
 class Tuned(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("buckets_per_level", ctypes.c_uint32 * 8),
                 ("overpartition_b", ctypes.c_uint32), ("candidates", ctypes.c_uint32),
-                ("ms", ctypes.c_float)]
+                ("ms", ctypes.c_float), ("oversample_a", ctypes.c_uint32), ("basecase_cap", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -110,6 +110,7 @@ _SIGS = {
     "ams_step_partition": (_ST, [_P, _P, _P, _P, _U64, _I, _P, _U32, _P]),
     "ams_step_base_case": (_ST, [_P, _P, _U64, _I, _P]),
     "ams_sort_small_noalloc": (_ST, [_P, _P, _U64, _I, _P]),
+    "ams_rlm_sort": (_ST, [_P, _P, _P, _P, _P, _U64, _I, _U32, _I, _PU32, _U64, _P]),
     "ams_tune": (_ST, [_P, _U64, _I, _I, _P, ctypes.POINTER(Tuned)]),
     "ams_server_create": (_ST, [_U64, _I, _U64, ctypes.POINTER(ctypes.c_void_p)]),
     "ams_server_reserve": (_ST, [_P, ctypes.POINTER(Request)]),
@@ -388,14 +389,30 @@ def request_scratch_bytes(n, kt, levels=2, buckets=(256, 256), a=0, b=0, cap=0, 
     return int(lib().ams_request_scratch_bytes(ctypes.byref(rq)))
 
 
+def rlm_sort(keys_in, keys_out=None, vals_in=None, vals_out=None, run=8192, parts=(64, 64), seed=0,
+             kt=None, ctx=None, stream=None):
+    """RLM-sort (ams_rlm_sort, Section 5): same result as the sample sort calls."""
+    keys_out = keys_in if keys_out is None else keys_out
+    if vals_in is not None and vals_out is None:
+        vals_out = vals_in
+    pk = _buckets(parts) if len(parts) else None
+    h = ctx.handle if ctx is not None else None
+    _check(lib().ams_rlm_sort(h, _dev(keys_in), _dev(keys_out), _dev(vals_in) if vals_in is not None else None,
+                              _dev(vals_out) if vals_out is not None else None, keys_in.numel(),
+                              key_type(keys_in, kt), run, len(parts), pk, seed, _stream(stream)),
+           "ams_rlm_sort")
+    return keys_out if vals_in is None else (keys_out, vals_out)
+
+
 def tune(n, kt, pairs=False, ctx=None, stream=None) -> dict:
     """The autotuner's plan for n keys of type kt (ams_tune): levels, buckets (r per
-    level), b, and its time on synthetic keys."""
+    level), b, a, cap (0 = defaults), and its score on synthetic keys.  The keys
+    levels / buckets / b / a / cap can be passed to the sort calls as they are."""
     t = Tuned()
     h = ctx.handle if ctx is not None else None
     _check(lib().ams_tune(h, n, kt, 1 if pairs else 0, _stream(stream), ctypes.byref(t)), "ams_tune")
     return {"levels": t.levels, "buckets": list(t.buckets_per_level)[:t.levels], "b": t.overpartition_b,
-            "candidates": t.candidates, "ms": t.ms}
+            "a": t.oversample_a, "cap": t.basecase_cap, "candidates": t.candidates, "ms": t.ms}
 
 
 class Server:

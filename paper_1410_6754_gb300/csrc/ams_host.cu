@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "ams_internal.cuh"
+#include "rlm.cuh"
 
 namespace ams {
 
@@ -30,7 +31,7 @@ struct Plan {
   int ksize = 8;
   bool pairs = false;
   uint64_t n = 0, nseg_user = 1;
-  uint64_t seg1_cap = 0, bc0_cap = 0, big_cap = 0;
+  uint64_t seg1_cap = 0, bc0_cap = 0, big_cap = 0, tiny_cap = 0;
   LevelPlan lv[kMaxLevels];
 };
 
@@ -74,6 +75,7 @@ ams_status make_plan(uint64_t n, uint64_t nseg_user, ams_key_type kt, bool pairs
   const uint64_t big = n / (C + 1) + 1;  // segments larger than C that fit in n
   p->seg1_cap = std::min<uint64_t>(nseg_user, big);
   p->bc0_cap = std::min<uint64_t>(nseg_user, n) + 1;
+  p->tiny_cap = p->bc0_cap;
   p->big_cap = big;
   uint64_t nseg_cap = p->seg1_cap;
   const uint64_t chunk_goal = (n + (uint64_t)sm_count * 8 - 1) / ((uint64_t)sm_count * 8);
@@ -135,6 +137,7 @@ struct Bufs {
   uint32_t* status;
   Seg* segs1;
   BcItem* bc0;
+  BcItem* tiny;
   BcItem* big;
   uint16_t* ids;  // bucket id of every key (rewritten by each level)
   LevelBufs lv[kMaxLevels];
@@ -149,6 +152,7 @@ size_t carve(const Plan& p, char* base, Bufs* b) {
   b->vtmp = p.pairs ? c.take<uint64_t>(p.n) : nullptr;
   b->segs1 = c.take<Seg>(p.seg1_cap + 1);
   b->bc0 = c.take<BcItem>(p.bc0_cap);
+  b->tiny = c.take<BcItem>(p.tiny_cap);
   b->big = c.take<BcItem>(p.big_cap + 1);
   for (int l = 0; l < p.L; ++l) {
     const LevelPlan& lp = p.lv[l];
@@ -199,6 +203,12 @@ struct Context {
   // step calls
   char* step_ws = nullptr;
   size_t step_bytes = 0;
+  // RLM-sort tables (pinned staging; the event marks the end of the last copy)
+  void* rlm_host = nullptr;
+  size_t rlm_host_bytes = 0;
+  cudaEvent_t rlm_done = nullptr;
+  cudaStream_t rlm_stream = nullptr;
+  bool rlm_pending = false;
   std::mutex mu;
 };
 
@@ -340,10 +350,12 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
   ia.need_copy_small = (!inplace || f32) ? 1 : 0;
   ia.segs1 = b.segs1;
   ia.bc0 = b.bc0;
+  ia.tiny = b.tiny;
   ia.ctr0 = &b.ctr[0];
   ia.status = b.status;
   ia.seg_cap = (uint32_t)p.seg1_cap;
   ia.bc_cap = (uint32_t)p.bc0_cap;
+  ia.tiny_cap = (uint32_t)p.tiny_cap;
   const int init_grid = (int)std::min<uint64_t>((nseg_user + 255) / 256, (uint64_t)SM * 8);
   ln.begin(AMS_K_INIT);
   AMS_TRY(ln.end(launch_init(ia, init_grid, s)));
@@ -376,6 +388,18 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
   if ((st = run_basecase(rq->keys_in, rq->vals_in, b.bc0, &b.ctr[0].n_bc, f32 ? 1 : 0, p.bc0_cap,
                          false)) != AMS_OK)
     return st;
+  {
+    // user segments of at most kTiny keys: one warp each (all-pairs ranks)
+    BaseArgs ta = ba;
+    ta.src = rq->keys_in;
+    ta.vsrc = rq->vals_in;
+    ta.items = b.tiny;
+    ta.nitems = &b.ctr[0].n_tiny;
+    ta.tf_load = f32 ? 1 : 0;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((p.tiny_cap + 15) / 16, (uint64_t)SM * 4));
+    ln.begin(AMS_K_BASECASE);
+    AMS_TRY(ln.end(launch_tiny(ta, p.ksize, p.pairs, grid, s)));
+  }
 
   LevelArgs la{};
   fill_thr(la.a_thr);
@@ -731,6 +755,11 @@ ams_status ams_context_destroy(void* ctx) {
   if (cx->stage) cudaFree(cx->stage);
   if (cx->step_ws) cudaFree(cx->step_ws);
   for (cudaEvent_t e : cx->ev_pool) cudaEventDestroy(e);
+  if (cx->rlm_done) {
+    cudaEventSynchronize(cx->rlm_done);
+    cudaEventDestroy(cx->rlm_done);
+  }
+  if (cx->rlm_host) cudaFreeHost(cx->rlm_host);
   delete cx;
   return AMS_OK;
 }
@@ -821,6 +850,178 @@ ams_status ams_get_stats(void* ctx, ams_stats* out) {
   cx->ev_used = 0;
   cx->ev_kind.clear();
   return AMS_OK;
+}
+
+// ------------------------------------------------------------------------ RLM-sort
+// Section 5 on one GPU: tiles of `run` positions play the processing elements.  The
+// part boundaries of every level are fixed by n and the part counts (part j of a part
+// of m elements starts floor(j m / r) after it), so the host plans them, together
+// with the tile lists the base-case kernel sorts: level 0 the tiles of the input,
+// level l the tiles of every level-l part after its delivery (the local merge).
+static ams_status run_rlm(Context* cx, const void* kin, void* kout, const uint64_t* vin, uint64_t* vout,
+                          uint64_t n, ams_key_type kt, uint32_t run, int levels, const uint32_t* parts,
+                          uint64_t seed, cudaStream_t s) {
+  if (kt != AMS_U32 && kt != AMS_U64 && kt != AMS_F32) return AMS_ERR_INVALID;
+  const bool pairs = vin != nullptr || vout != nullptr;
+  if (pairs && (!vin || !vout)) return AMS_ERR_INVALID;
+  if (n == 0) return AMS_OK;
+  if (!kin || !kout || n >= 0xFFFFFFFFull || levels < 0 || levels > kMaxLevels) return AMS_ERR_INVALID;
+  if (levels > 0 && !parts) return AMS_ERR_INVALID;
+  const int ks = ksize_of(kt);
+  if (((uintptr_t)kin % ks) || ((uintptr_t)kout % ks) || ((uintptr_t)vin % 8) || ((uintptr_t)vout % 8))
+    return AMS_ERR_INVALID;
+  if (run < 2 || run > basecase_max_cap(ks, pairs)) return AMS_ERR_UNSUPPORTED;
+  // part boundaries per level (level 0: the whole input)
+  std::vector<std::vector<uint32_t>> plo(levels + 1);
+  plo[0] = {0u, (uint32_t)n};
+  for (int l = 1; l <= levels; ++l) {
+    const uint32_t r = parts[l - 1];
+    if (r < 2 || r > 65536) return AMS_ERR_INVALID;
+    const std::vector<uint32_t>& up = plo[l - 1];
+    std::vector<uint32_t>& lo = plo[l];
+    if ((up.size() - 1) * (uint64_t)r > (1u << 24)) return AMS_ERR_UNSUPPORTED;
+    for (size_t q = 0; q + 1 < up.size(); ++q) {
+      const uint64_t m = up[q + 1] - up[q];
+      for (uint32_t j = 0; j < r; ++j) lo.push_back(up[q] + (uint32_t)((j * m) / r));
+    }
+    lo.push_back((uint32_t)n);
+  }
+  // the last level's parts must fit one tile (they are finished by its local merge)
+  for (size_t q = 0; q + 1 < plo[levels].size(); ++q)
+    if (plo[levels][q + 1] - plo[levels][q] > run) return AMS_ERR_UNSUPPORTED;
+  // tiles of every level's parts, and the largest tile count of a part per level
+  std::vector<std::vector<BcItem>> items(levels + 1);
+  std::vector<uint32_t> max_tiles(levels + 1, 0);
+  for (int l = 0; l <= levels; ++l) {
+    for (size_t q = 0; q + 1 < plo[l].size(); ++q) {
+      uint32_t t = 0;
+      for (uint32_t b = plo[l][q]; b < plo[l][q + 1]; b += run, ++t)
+        items[l].push_back(BcItem{b, std::min(plo[l][q + 1], b + run), BC_SORT, 0});
+      max_tiles[l] = std::max(max_tiles[l], t);
+    }
+  }
+  for (int l = 0; l < levels; ++l)
+    if ((size_t)max_tiles[l] * 6 + 16 > 200u * 1024) return AMS_ERR_UNSUPPORTED;  // select windows
+  // workspace: status, temporary keys (and payloads), per level part bounds, item
+  // counts and items, cut table (largest level)
+  size_t cut_words = 0;
+  for (int l = 1; l <= levels; ++l)
+    cut_words = std::max(cut_words, (plo[l - 1].size() - 1) * (size_t)(parts[l - 1] + 1) * max_tiles[l - 1]);
+  auto lay = [&](char* base, Bufs& bb, std::vector<uint32_t*>& d_plo, std::vector<uint32_t*>& d_cnt,
+                 std::vector<BcItem*>& d_items, uint32_t*& d_cuts) {
+    Carver c{base};
+    bb.status = c.take<uint32_t>(64);
+    bb.tmp = c.take<char>(n * ks);
+    bb.vtmp = pairs ? c.take<uint64_t>(n) : nullptr;
+    d_plo.assign(levels + 1, nullptr);
+    d_cnt.assign(levels + 1, nullptr);
+    d_items.assign(levels + 1, nullptr);
+    for (int l = 0; l <= levels; ++l) {
+      d_plo[l] = c.take<uint32_t>(plo[l].size());
+      d_cnt[l] = c.take<uint32_t>(1);
+      d_items[l] = c.take<BcItem>(items[l].size());
+    }
+    d_cuts = c.take<uint32_t>(cut_words + 1);
+    return c.off + 256;
+  };
+  Bufs bb{};
+  std::vector<uint32_t*> d_plo, d_cnt;
+  std::vector<BcItem*> d_items;
+  uint32_t* d_cuts = nullptr;
+  const size_t need = lay(nullptr, bb, d_plo, d_cnt, d_items, d_cuts);
+  ams_status st = ensure_ws(cx, need);
+  if (st != AMS_OK) return st;
+  lay(cx->ws, bb, d_plo, d_cnt, d_items, d_cuts);
+  cx->has_run = false;  // (the level statistics describe AMS-sort runs)
+  cx->last_stream = s;
+  // tables to the device through a pinned staging buffer owned by the context
+  size_t hb = 0;
+  for (int l = 0; l <= levels; ++l) hb += plo[l].size() * 4 + 4 + items[l].size() * sizeof(BcItem) + 16;
+  if (cx->rlm_host_bytes < hb) {
+    if (cx->rlm_host) {
+      AMS_TRY(cudaStreamSynchronize(cx->rlm_stream ? cx->rlm_stream : s));
+      cudaFreeHost(cx->rlm_host);
+      cx->rlm_host = nullptr;
+      cx->rlm_host_bytes = 0;
+    }
+    if (cudaMallocHost(&cx->rlm_host, hb) != cudaSuccess) {
+      cudaGetLastError();
+      return AMS_ERR_OOM;
+    }
+    cx->rlm_host_bytes = hb;
+  } else if (cx->rlm_pending) {
+    AMS_TRY(cudaEventSynchronize(cx->rlm_done));  // the previous copy out of the staging buffer
+  }
+  char* h = (char*)cx->rlm_host;
+  for (int l = 0; l <= levels; ++l) {
+    std::memcpy(h, plo[l].data(), plo[l].size() * 4);
+    AMS_TRY(cudaMemcpyAsync(d_plo[l], h, plo[l].size() * 4, cudaMemcpyHostToDevice, s));
+    h += plo[l].size() * 4;
+    const uint32_t cnt = (uint32_t)items[l].size();
+    std::memcpy(h, &cnt, 4);
+    AMS_TRY(cudaMemcpyAsync(d_cnt[l], h, 4, cudaMemcpyHostToDevice, s));
+    h += 4;
+    std::memcpy(h, items[l].data(), items[l].size() * sizeof(BcItem));
+    AMS_TRY(cudaMemcpyAsync(d_items[l], h, items[l].size() * sizeof(BcItem), cudaMemcpyHostToDevice, s));
+    h += items[l].size() * sizeof(BcItem) + 16;
+  }
+  if (!cx->rlm_done) AMS_TRY(cudaEventCreateWithFlags(&cx->rlm_done, cudaEventDisableTiming));
+  AMS_TRY(cudaEventRecord(cx->rlm_done, s));
+  cx->rlm_pending = true;
+  cx->rlm_stream = s;
+
+  const bool f32 = kt == AMS_F32;
+  const int SM = cx->sm_count;
+  Launcher ln{cx, s};
+  // buffers: level l's tiles live in X_l; X_levels is the output
+  auto X = [&](int l) -> void* { return ((levels - l) % 2 == 0) ? kout : bb.tmp; };
+  auto V = [&](int l) -> uint64_t* { return ((levels - l) % 2 == 0) ? vout : bb.vtmp; };
+  auto sort_tiles = [&](int l, const void* src, const uint64_t* vsrc) -> ams_status {
+    BaseArgs ba{};
+    ba.src = src;
+    ba.out = X(l);
+    ba.vsrc = vsrc;
+    ba.vout = pairs ? V(l) : nullptr;
+    ba.items = d_items[l];
+    ba.nitems = d_cnt[l];
+    ba.tf_load = (l == 0 && f32) ? 1 : 0;
+    ba.tf_store = (l == levels && f32) ? 1 : 0;
+    ba.status = bb.status;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(items[l].size(), (uint64_t)SM * 8));
+    ln.begin(AMS_K_BASECASE);
+    return cuda_status(ln.end(launch_basecase(ba, ks, pairs, false, grid, s)));
+  };
+  if ((st = sort_tiles(0, kin, vin)) != AMS_OK) return st;
+  for (int l = 1; l <= levels; ++l) {
+    RlmArgs ra{};
+    ra.src = X(l - 1);
+    ra.dst = X(l);
+    ra.vsrc = pairs ? V(l - 1) : nullptr;
+    ra.vdst = pairs ? V(l) : nullptr;
+    ra.part_lo = d_plo[l - 1];
+    ra.nparts = (uint32_t)(plo[l - 1].size() - 1);
+    ra.r = parts[l - 1];
+    ra.run = run;
+    ra.max_tiles = std::max<uint32_t>(1, max_tiles[l - 1]);
+    ra.cuts = d_cuts;
+    ra.seed = seed;
+    ra.level = l;
+    ra.status = bb.status;
+    ln.begin(AMS_K_SCATTER);
+    AMS_TRY(ln.end(launch_rlm_level(ra, ks, pairs, SM, s)));
+    if ((st = sort_tiles(l, X(l), pairs ? V(l) : nullptr)) != AMS_OK) return st;
+  }
+  return AMS_OK;
+}
+
+ams_status ams_rlm_sort(void* ctx, const void* d_keys_in, void* d_keys_out, const uint64_t* d_vals_in,
+                        uint64_t* d_vals_out, uint64_t n, ams_key_type kt, uint32_t run, int levels,
+                        const uint32_t* parts_per_level, uint64_t seed, void* stream) {
+  Context* cx = ctx_or_default(ctx);
+  if (!cx) return AMS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(cx->mu);
+  return run_rlm(cx, d_keys_in, d_keys_out, d_vals_in, d_vals_out, n, kt, run, levels, parts_per_level, seed,
+                 (cudaStream_t)stream);
 }
 
 // ------------------------------------------------------------- level intermediates

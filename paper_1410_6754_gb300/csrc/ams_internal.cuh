@@ -28,6 +28,7 @@ constexpr uint32_t kCopyChunk = 65536;  // elements per copy work item
 constexpr int kMaxBuckets = 2048;       // largest b*r per level
 constexpr uint32_t kCellTable = 16384;  // cells of the table classifier
 constexpr int kThrCount = 48;           // oversampling thresholds 10^(a/1.6)
+constexpr uint32_t kTiny = 256;         // user segments up to this size: one warp, all-pairs ranks
 
 // base-case work item kinds
 enum : uint32_t { BC_SORT = 0, BC_COPY = 1, BC_BIG = 2 };
@@ -60,7 +61,8 @@ struct LevelCounters {
   uint32_t keys;       // keys in this level's segments
   uint32_t bc_keys;    // keys in this level's base-case items
   uint32_t n_big;      // groups above capacity after the last level
-  uint32_t pad[2];
+  uint32_t n_tiny;     // level 0: user segments of at most kTiny keys (warp rank sort)
+  uint32_t pad;
 };
 
 struct LevelArgs {
@@ -118,9 +120,10 @@ struct InitArgs {
   int need_copy_small;  // 1: singleton segments still need a copy / untransform
   Seg* segs1;
   BcItem* bc0;
+  BcItem* tiny;         // segments of 2..kTiny keys (or 1 key needing a copy)
   LevelCounters* ctr0;
   uint32_t* status;
-  uint32_t seg_cap, bc_cap;
+  uint32_t seg_cap, bc_cap, tiny_cap;
 };
 
 struct BaseArgs {
@@ -215,6 +218,9 @@ cudaError_t launch_binpack(const LevelArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_scatter(const LevelArgs& a, int ksize, bool pairs, bool stable, int grid,
                            cudaStream_t s);
 cudaError_t launch_basecase(const BaseArgs& a, int ksize, bool pairs, bool big, int grid, cudaStream_t s);
+cudaError_t launch_tiny(const BaseArgs& a, int ksize, bool pairs, int grid, cudaStream_t s);
+struct RlmArgs;
+cudaError_t launch_rlm_level(const RlmArgs& a, int ksize, bool pairs, int sm_count, cudaStream_t s);
 
 // shared-memory bytes each kernel needs (for occupancy and opt-in)
 size_t scatter_smem_bytes(int ksize, bool pairs, bool stable, uint32_t B);

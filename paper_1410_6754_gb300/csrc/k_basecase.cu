@@ -23,6 +23,7 @@ struct BaseCfg {
   static constexpr uint32_t CELLS = 16384;  // 16-bit counters, two per word
   static constexpr uint32_t BIGCELL = 8;    // cells above this size are checked for one value
   static constexpr uint32_t SKEWCELL = 32;  // a cell above this size with two values: bitonic
+  static constexpr uint32_t LIST = CAP / 4;  // cells of two or more keys listed (else ranked per slot)
   // two blocks per SM when their shared memory fits (keys only)
   static constexpr int MINB = PAIRS ? 1 : 2;
 };
@@ -34,8 +35,10 @@ struct BaseSmem {
   uint16_t* pos;   // input index of each slot (pairs: the stable tiebreak)
   uint64_t* vals;  // payloads by input index
   K* red;          // 3 * (NT/32) keys: min / max, scan totals
-  uint32_t* flag;  // [0]: some cell holds more than BIGCELL keys
+  uint32_t* flag;  // [0]: some cell holds more than BIGCELL keys; [1]: skewed item;
+                   // [2]: cells holding two or more keys (entries of `shared`)
   uint32_t* mixed; // one bit per cell: the cell holds more than one key value
+  uint16_t* shared;  // cells holding two or more keys (at most LIST)
 };
 
 template <typename K, bool PAIRS>
@@ -43,23 +46,24 @@ __host__ __device__ constexpr size_t base_smem_layout(size_t* off) {
   using C = BaseCfg<K, PAIRS>;
   size_t o = 0;
   off[0] = o; o += (size_t)C::CAP * sizeof(K);                          // keys
-  off[1] = o; o += (size_t)C::CELLS * 2;                                // cells
+  off[1] = o; o += (size_t)C::CELLS * 2 + 16;                           // cells (+ end)
   off[2] = o; o += PAIRS ? (size_t)C::CAP * 2 : 0;                      // pos
   o = (o + 15) & ~(size_t)15;
   off[3] = o; o += PAIRS ? (size_t)C::CAP * 8 : 0;                      // payloads
   off[4] = o; o += (size_t)3 * (C::NT / 32) * sizeof(uint64_t);         // red / scan
   off[5] = o; o += 16;                                                   // flag
   off[6] = o; o += (size_t)C::CELLS / 8;                                 // mixed bits
+  off[7] = o; o += (size_t)C::LIST * 2;                                  // shared cells
   return o;
 }
 
 template <typename K, bool PAIRS>
 __device__ __forceinline__ BaseSmem<K> base_smem(unsigned char* smem) {
-  size_t off[7];
+  size_t off[8];
   base_smem_layout<K, PAIRS>(off);
   return BaseSmem<K>{(K*)(smem + off[0]), (uint32_t*)(smem + off[1]), (uint16_t*)(smem + off[2]),
                      (uint64_t*)(smem + off[3]), (K*)(smem + off[4]), (uint32_t*)(smem + off[5]),
-                     (uint32_t*)(smem + off[6])};
+                     (uint32_t*)(smem + off[6]), (uint16_t*)(smem + off[7])};
 }
 
 // 16-bit cell counter c (two per 32-bit word; every count, prefix and end is <= CAP)
@@ -262,15 +266,16 @@ __device__ __forceinline__ void sort_loaded(K (&x)[BaseCfg<K, PAIRS>::KPT], K* d
   const CellMap<K> cell{kmin, sh, scale};
   const uint32_t nv = M / 8;  // 128-bit words of counters
   for (uint32_t i = tid; i < nv; i += NT) ((uint4*)sm.cw)[i] = make_uint4(0, 0, 0, 0);
-  if (tid == 0) sm.flag[0] = sm.flag[1] = 0;
+  if (tid == 0) sm.flag[0] = sm.flag[1] = sm.flag[2] = 0;
   __syncthreads();
+  // count the cells; the count a key's atomic returns is its arrival rank in its cell
+  uint32_t rr[(KPT + 1) / 2];  // ranks, 16 bits per key
+#pragma unroll
+  for (int i = 0; i < (KPT + 1) / 2; ++i) rr[i] = 0;
 #pragma unroll
   for (int q = 0; q < KPT; ++q) {
     if ((uint32_t)q * NT >= m) break;
-    if (tid + q * NT < m) {
-      const uint32_t c = cell(x[q]);
-      atomicAdd(&sm.cw[c >> 1], 1u << ((c & 1) << 4));
-    }
+    if (tid + q * NT < m) rr[q >> 1] |= cell_add(sm.cw, cell(x[q])) << ((q & 1) << 4);
   }
   __syncthreads();
   // exclusive scan of the M 16-bit counters in one pass: thread t owns the 128-bit
@@ -311,16 +316,25 @@ __device__ __forceinline__ void sort_loaded(K (&x)[BaseCfg<K, PAIRS>::KPT], K* d
       u.w = pre(u.w);
       cv[i] = u;
     }
+    if (tid == 0) c16[M] = (uint16_t)m;  // cell c spans [c16[c], c16[c+1])
   }
   __syncthreads();
+  // every key to its slot: cell start + arrival rank.  A key alone in its cell is then
+  // at its final place; the second arrival of a cell lists the cell for sorting.
 #pragma unroll
   for (int q = 0; q < KPT; ++q) {
     if ((uint32_t)q * NT >= m) break;
     const uint32_t e = tid + q * NT;
     if (e < m) {
-      const uint32_t s = cell_add(sm.cw, cell(x[q]));  // afterwards: the cell's end
+      const uint32_t c = cell(x[q]);
+      const uint32_t r = (rr[q >> 1] >> ((q & 1) << 4)) & 0xFFFFu;
+      const uint32_t s = c16[c] + r;
       sm.keys[s] = x[q];
       if constexpr (PAIRS) sm.pos[s] = (uint16_t)e;
+      if (r == 1) {
+        const uint32_t i = atomicAdd(&sm.flag[2], 1u);
+        if (i < C::LIST) sm.shared[i] = (uint16_t)c;
+      }
     }
   }
   next();  // the keys are in shared memory now
@@ -335,7 +349,7 @@ __device__ __forceinline__ void sort_loaded(K (&x)[BaseCfg<K, PAIRS>::KPT], K* d
     for (uint32_t s = tid; s < m; s += NT) {
       const K v = sm.keys[s];
       const uint32_t c = cell(v);
-      const uint32_t cb = c ? c16[c - 1] : 0u, ce = c16[c];
+      const uint32_t cb = c16[c], ce = c16[c + 1];
       if (ce - cb > C::BIGCELL && sm.keys[cb] != v) {
         atomicOr(&sm.mixed[c >> 5], 1u << (c & 31));
         if (ce - cb > C::SKEWCELL) sm.flag[1] = 1;
@@ -350,11 +364,44 @@ __device__ __forceinline__ void sort_loaded(K (&x)[BaseCfg<K, PAIRS>::KPT], K* d
       return;
     }
   }
+  if (!big && sm.flag[2] <= C::LIST) {
+    // usual case: sort the listed cells (at most BIGCELL keys each) in place, one
+    // thread per cell (insertion sort; pairs by (key, input index), so stable), then
+    // copy the sorted item out with coalesced stores
+    const uint32_t nshared = sm.flag[2];
+    for (uint32_t i = tid; i < nshared; i += NT) {
+      const uint32_t c = sm.shared[i];
+      const uint32_t cb = c16[c], ce = c16[c + 1];
+      for (uint32_t j = cb + 1; j < ce; ++j) {
+        const K v = sm.keys[j];
+        uint32_t p = 0;
+        if constexpr (PAIRS) p = sm.pos[j];
+        uint32_t t = j;
+        while (t > cb) {
+          const K y = sm.keys[t - 1];
+          bool gt = y > v;
+          if constexpr (PAIRS) gt = gt || (y == v && sm.pos[t - 1] > p);
+          if (!gt) break;
+          sm.keys[t] = y;
+          if constexpr (PAIRS) sm.pos[t] = sm.pos[t - 1];
+          --t;
+        }
+        sm.keys[t] = v;
+        if constexpr (PAIRS) sm.pos[t] = (uint16_t)p;
+      }
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < m; i += NT) {
+      dst[b + i] = order_out<K>(sm.keys[i], tf_out);
+      if constexpr (PAIRS) vdst[b + i] = sm.vals[sm.pos[i]];
+    }
+    return;
+  }
   auto rank_all = [&](auto one_value_check) {
     for (uint32_t s = tid; s < m; s += NT) {
       const K v = sm.keys[s];
       const uint32_t c = cell(v);
-      const uint32_t cb = c ? c16[c - 1] : 0u, ce = c16[c];
+      const uint32_t cb = c16[c], ce = c16[c + 1];
       if (ce - cb == 1) {  // alone in its cell: its place is the cell start
         dst[b + cb] = order_out<K>(v, tf_out);
         if constexpr (PAIRS) vdst[b + cb] = sm.vals[sm.pos[s]];
@@ -511,8 +558,72 @@ __global__ void __launch_bounds__(512) k_bigsort(BaseArgs a) {
   }
 }
 
+// ------------------------------------------------------------------- tiny segments
+// User segments of at most kTiny keys: one warp per segment, the fast work-inefficient
+// sort of Section 4.2 on the warp -- element e's final place is the number of elements
+// (key, index) ordered before it, counted against every element of the segment (read
+// from shared memory, where the whole warp reads one element at a time: a broadcast).
+// Many segments per block, no block barrier.
+template <typename K, bool PAIRS>
+__global__ void __launch_bounds__(512, 2) k_tiny(BaseArgs a) {
+  constexpr int NW = 16, J = kTiny / 32;
+  __shared__ K sk[NW][kTiny];
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t nitems = *a.nitems;
+  const K* src = (const K*)a.src;
+  K* out = (K*)a.out;
+  for (uint32_t it = blockIdx.x * NW + w; it < nitems; it += gridDim.x * NW) {
+    const BcItem item = a.items[it];
+    const uint32_t b = item.begin, m = min(item.end - item.begin, kTiny);
+    K x[J];
+    uint64_t v[PAIRS ? J : 1];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      if ((uint32_t)j * 32 >= m) break;  // (uniform)
+      const uint32_t e = lane + 32 * j;
+      if (e < m) {
+        x[j] = order_in<K>(src[b + e], a.tf_load);
+        sk[w][e] = x[j];
+        if constexpr (PAIRS) v[j] = a.vsrc[b + e];
+      }
+    }
+    __syncwarp();
+    uint32_t r[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) r[j] = 0;
+    for (uint32_t t = 0; t < m; ++t) {
+      const K y = sk[w][t];
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        if ((uint32_t)j * 32 >= m) break;
+        r[j] += (y < x[j]) | ((y == x[j]) & (t < lane + 32 * j));
+      }
+    }
+    __syncwarp();  // every read of sk (and of src) is done before the stores
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      if ((uint32_t)j * 32 >= m) break;
+      const uint32_t e = lane + 32 * j;
+      if (e < m) {
+        out[b + r[j]] = order_out<K>(x[j], a.tf_store);
+        if constexpr (PAIRS) a.vout[b + r[j]] = v[j];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_tiny(const BaseArgs& a, int ksize, bool pairs, int grid, cudaStream_t s) {
+  if (ksize == 4) {
+    if (pairs) k_tiny<uint32_t, true><<<grid, 512, 0, s>>>(a); else k_tiny<uint32_t, false><<<grid, 512, 0, s>>>(a);
+  } else {
+    if (pairs) k_tiny<uint64_t, true><<<grid, 512, 0, s>>>(a); else k_tiny<uint64_t, false><<<grid, 512, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
 size_t basecase_smem_bytes(int ksize, bool pairs) {
-  size_t off[7];
+  size_t off[8];
   if (ksize == 4) return pairs ? base_smem_layout<uint32_t, true>(off) : base_smem_layout<uint32_t, false>(off);
   return pairs ? base_smem_layout<uint64_t, true>(off) : base_smem_layout<uint64_t, false>(off);
 }

@@ -345,25 +345,50 @@ __global__ void __launch_bounds__(512, 2) k_binpack(LevelArgs a) {
 }
 
 // ----------------------------------------------------------------------------- init
-// User segments larger than C become level-1 segments; the others are base-case
-// items (a single key needs work only when it must be copied or untransformed).
+// User segments larger than C become level-1 segments, those of at most kTiny keys go
+// to the warp rank sort, the others are base-case items (a single key needs work
+// only when it must be copied or untransformed).  Each block of 256 segments reserves
+// its table entries with one atomic per table (block scans of the counts).
 __global__ void __launch_bounds__(256) k_init(InitArgs a) {
-  for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < a.nseg;
-       s += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t b = a.offsets ? (uint32_t)a.offsets[s] : 0u;
-    const uint32_t e = a.offsets ? (uint32_t)a.offsets[s + 1] : a.n;
-    if (e <= b) continue;
-    const uint32_t m = e - b;
-    if (m > a.C) {
-      const uint32_t i = atomicAdd(&a.ctr0->nseg_next, 1u);
+  constexpr int NT = 256;
+  __shared__ uint32_t ws[NT / 32 + 1];
+  __shared__ uint32_t base[3];
+  for (uint64_t s0 = blockIdx.x * (uint64_t)NT; s0 < a.nseg; s0 += (uint64_t)gridDim.x * NT) {
+    const uint64_t s = s0 + threadIdx.x;
+    uint32_t b = 0, e = 0, kind = 3;  // 0 level-1 segment, 1 tiny, 2 base case, 3 nothing
+    if (s < a.nseg) {
+      b = a.offsets ? (uint32_t)a.offsets[s] : 0u;
+      e = a.offsets ? (uint32_t)a.offsets[s + 1] : a.n;
+      const uint32_t m = e > b ? e - b : 0u;
+      if (m > a.C) kind = 0;
+      else if (m > 1 || (m == 1 && a.need_copy_small)) kind = m <= kTiny ? 1 : 2;
+    }
+    uint32_t tot[4];
+    const uint32_t o_seg = block_exclusive_scan<NT, uint32_t>(kind == 0, ws, tot[0]);
+    const uint32_t o_tiny = block_exclusive_scan<NT, uint32_t>(kind == 1, ws, tot[1]);
+    const uint32_t o_bc = block_exclusive_scan<NT, uint32_t>(kind == 2, ws, tot[2]);
+    block_exclusive_scan<NT, uint32_t>(kind == 2 ? e - b : 0u, ws, tot[3]);
+    if (threadIdx.x == 0) {
+      base[0] = tot[0] ? atomicAdd(&a.ctr0->nseg_next, tot[0]) : 0u;
+      base[1] = tot[1] ? atomicAdd(&a.ctr0->n_tiny, tot[1]) : 0u;
+      base[2] = tot[2] ? atomicAdd(&a.ctr0->n_bc, tot[2]) : 0u;
+      if (tot[3]) atomicAdd(&a.ctr0->bc_keys, tot[3]);
+    }
+    __syncthreads();
+    if (kind == 0) {
+      const uint32_t i = base[0] + o_seg;
       if (i < a.seg_cap) a.segs1[i] = Seg{b, e};
       else atomicOr(a.status, ST_OVERFLOW);
-    } else if (m > 1 || a.need_copy_small) {
-      const uint32_t i = atomicAdd(&a.ctr0->n_bc, 1u);
-      atomicAdd(&a.ctr0->bc_keys, m);
+    } else if (kind == 1) {
+      const uint32_t i = base[1] + o_tiny;
+      if (i < a.tiny_cap) a.tiny[i] = BcItem{b, e, BC_SORT, 0};
+      else atomicOr(a.status, ST_OVERFLOW);
+    } else if (kind == 2) {
+      const uint32_t i = base[2] + o_bc;
       if (i < a.bc_cap) a.bc0[i] = BcItem{b, e, BC_SORT, 0};
       else atomicOr(a.status, ST_OVERFLOW);
     }
+    __syncthreads();  // (base is rewritten by the next batch)
   }
 }
 

@@ -63,7 +63,8 @@ def test_struct_layouts_match_header(tmp_path):
                                       "n", "kt", "levels", "buckets_per_level", "seed", "opt"]),
         "ams_stats": (ams.Stats, ["levels_planned", "kernel_launches", "segments", "basecase_items",
                                   "device_status", "kernel_ms", "kernel_calls", "kernel_elems"]),
-        "ams_tuned": (ams.Tuned, ["levels", "buckets_per_level", "overpartition_b", "candidates", "ms"]),
+        "ams_tuned": (ams.Tuned, ["levels", "buckets_per_level", "overpartition_b", "candidates", "ms",
+                                  "oversample_a", "basecase_cap"]),
         "ams_segment_info": (ams.SegmentInfo, ["begin", "end", "a", "S", "L", "ngroups", "npieces",
                                                "nbucket_ids"]),
     }

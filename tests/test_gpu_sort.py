@@ -142,6 +142,59 @@ def test_segmented(kt, bits, pairs):
     assert res is not None
 
 
+@pytest.mark.parametrize("kt,bits", [(O.KT_U32, 32), (O.KT_U64, 64), (O.KT_F32, 32)])
+@pytest.mark.parametrize("pairs", [False, True])
+@pytest.mark.parametrize("dist", ["uniform", "zipf"])
+def test_segmented_tiny_segments(kt, bits, pairs, dist):
+    """Many segments of at most 2^12 keys: those of at most 256 keys go through the warp
+    all-pairs rank sort, the others through the base case; every length from 0 to 300
+    appears (ties by original index with payloads = index), out of place and in place."""
+    rng = np.random.default_rng(kt * 7 + pairs + len(dist))
+    lens = np.concatenate([np.arange(0, 301), rng.integers(0, 4097, 200), [1, 1, 2, 255, 256, 257]])
+    rng.shuffle(lens)
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    n = int(off[-1])
+    if kt == O.KT_F32:
+        keys = I.normal_f32(n, 5)
+        if dist == "zipf":
+            keys = np.array([0.0, -0.0, 1.0, -1.0, 2.5], np.float32)[rng.integers(0, 5, n)]
+    else:
+        keys = I.generate(dist, n, 5, bits)
+    vals = np.arange(n, dtype=np.uint64)
+    ek = O.sort_segmented(kt, keys, off, vals if pairs else None)
+    do = to_dev(off.view(np.uint64))
+    # in place
+    dk, dv = to_dev(keys), to_dev(vals)
+    ams.sort_segmented(dk, do, vals=dv if pairs else None, levels=2, buckets=[16, 16], kt=kt)
+    ams.sync()
+    if pairs:
+        assert same_bits(to_np(dk, keys.dtype), ek[0])
+        assert np.array_equal(to_np(dv, np.uint64), ek[1])
+    else:
+        assert same_bits(to_np(dk, keys.dtype), ek)
+    # out of place, through a context
+    ctx = ams.Context()
+    kin, kout = to_dev(keys), torch.empty_like(to_dev(keys))
+    vin, vout = (to_dev(vals), torch.empty_like(to_dev(vals))) if pairs else (None, None)
+    ctx.sort(kin, kout, vin, vout, offsets=do, levels=2, buckets=[16, 16], kt=kt)
+    ctx.sync()
+    if pairs:
+        assert same_bits(to_np(kout, keys.dtype), ek[0])
+        assert np.array_equal(to_np(vout, np.uint64), ek[1])
+    else:
+        assert same_bits(to_np(kout, keys.dtype), ek)
+    assert same_bits(to_np(kin, keys.dtype), keys)  # the input is left alone
+    ctx.close()
+
+
+@pytest.mark.parametrize("kt,bits", [(O.KT_U32, 32), (O.KT_U64, 64), (O.KT_F32, 32)])
+@pytest.mark.parametrize("pairs", [False, True])
+def test_small_arrays_through_the_warp_sort(kt, bits, pairs):
+    for n in [2, 3, 31, 32, 33, 64, 100, 255, 256, 257]:
+        keys = I.normal_f32(n, n) if kt == O.KT_F32 else I.generate("zipf", n, n, bits)
+        _sort_check(keys, kt, 2, [64, 64], pairs=pairs)
+
+
 def test_out_of_place_and_host_entry_points():
     keys = I.generate("staggered", 1 << 20, 2, 64)
     src = to_dev(keys)

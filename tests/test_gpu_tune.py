@@ -22,7 +22,9 @@ def test_tuned_plan_sorts(kt, bits, pairs, lg):
     n = 1 << lg
     cfg = ams.tune(n, kt, pairs=pairs)
     assert 1 <= cfg["levels"] <= 3 and len(cfg["buckets"]) == cfg["levels"]
-    assert all(2 <= r <= 2048 for r in cfg["buckets"]) and cfg["b"] in (1, 4)
+    assert all(2 <= r <= 2048 for r in cfg["buckets"]) and cfg["b"] in (1, 4, 16, 64)
+    assert cfg["a"] in (0, 1) and cfg["cap"] in (0, ams.default_basecase_cap(kt, pairs) // 2)
+    assert cfg["b"] * cfg["buckets"][0] <= 2048
     assert cfg["ms"] > 0 and cfg["candidates"] >= 1
     assert ams.tune(n - 1, kt, pairs=pairs) == cfg  # same size class: cached
     keys = I.generate("uniform", n - 3, 4, bits)
@@ -30,12 +32,14 @@ def test_tuned_plan_sorts(kt, bits, pairs, lg):
     if pairs:
         vals = np.arange(len(keys), dtype=np.uint64)
         dv = to_dev(vals)
-        ams.sort_pairs(dk, dv, levels=cfg["levels"], buckets=cfg["buckets"], b=cfg["b"], kt=kt)
+        ams.sort_pairs(dk, dv, levels=cfg["levels"], buckets=cfg["buckets"], b=cfg["b"], a=cfg["a"],
+                       cap=cfg["cap"], kt=kt)
         ams.sync()
         ek, ev = O.sort_pairs(kt, keys, vals)
         assert np.array_equal(to_np(dv, np.uint64), ev)
     else:
-        ams.sort_keys(dk, levels=cfg["levels"], buckets=cfg["buckets"], b=cfg["b"], kt=kt)
+        ams.sort_keys(dk, levels=cfg["levels"], buckets=cfg["buckets"], b=cfg["b"], a=cfg["a"], cap=cfg["cap"],
+                      kt=kt)
         ams.sync()
         ek = O.sort_keys(kt, keys)
     assert same_bits(to_np(dk, keys.dtype), ek)

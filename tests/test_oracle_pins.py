@@ -457,6 +457,62 @@ def test_pieces_golden():
     assert n == 5
 
 
+# ----------------------------------------------------------------- RLM-sort (Section 5)
+def _brute_split(seqs, k):
+    """Split positions of rank k by listing every element as (key, sequence, position)
+    and sorting the tuples (Python's sort; no numpy)."""
+    els = sorted((int(v), i, j) for i, q in enumerate(seqs) for j, v in enumerate(q))
+    cnt = [0] * len(seqs)
+    for (_, i, _) in els[:k]:
+        cnt[i] += 1
+    return cnt
+
+
+def test_multiseq_select_brute_force():
+    """Section 4.1: the definition and the quickselect both equal the brute-force split
+    for every rank of small sorted sequences with many ties (and empty sequences)."""
+    rng = np.random.default_rng(31)
+    for trial in range(250):
+        p = int(rng.integers(1, 6))
+        seqs = [np.sort(rng.integers(0, 4, int(rng.integers(0, 7)))).astype(np.uint64) for _ in range(p)]
+        total = sum(len(q) for q in seqs)
+        for k in range(total + 1):
+            want = _brute_split(seqs, k)
+            assert O.multiseq_select_definition(seqs, k) == want
+            assert O.multiseq_select(seqs, k, seed=trial) == want
+
+
+def test_multiseq_select_hand_example():
+    # sequences (1 3 3 7), (3 5), (0 3): total order by (key, sequence, position):
+    # 0(s2) 1(s0) 3(s0) 3(s0) 3(s1) 3(s2) 5(s1) 7(s0)
+    seqs = [np.array([1, 3, 3, 7], np.uint64), np.array([3, 5], np.uint64), np.array([0, 3], np.uint64)]
+    want = {0: [0, 0, 0], 1: [0, 0, 1], 2: [1, 0, 1], 4: [3, 0, 1], 5: [3, 1, 1], 6: [3, 1, 2],
+            7: [3, 2, 2], 8: [4, 2, 2]}
+    for k, cut in want.items():
+        assert O.multiseq_select(seqs, k) == cut
+        assert O.multiseq_select_definition(seqs, k) == cut
+
+
+@pytest.mark.parametrize("dist", I.DISTRIBUTIONS)
+def test_rlm_sort_equals_definition(dist):
+    """Section 5: RLM-sort (runs sorted, parts by multisequence selection, pieces
+    delivered, local merge) gives the definition's output, and every part of every
+    level is perfectly balanced (sizes differ by at most one)."""
+    n = 6000
+    k = I.generate(dist, n, 13, 64)
+    v = np.arange(n, dtype=np.uint64)
+    tr = []
+    ok, ov = O.rlm_sort(O.KT_U64, k, 257, [5, 4], vals=v, trace=tr)
+    ek, ev = O.sort_pairs(O.KT_U64, k, v)
+    assert np.array_equal(ok, ek) and np.array_equal(ov, ev)
+    for t in tr:
+        sizes = np.diff(t["ranks"])
+        assert sizes.max() - sizes.min() <= 1
+        assert sum(t["cuts"][-1]) == t["end"] - t["begin"]
+    out = O.rlm_sort(O.KT_F32, I.normal_f32(3000, 2), 100, [7])
+    assert np.array_equal(out.view(np.uint32), O.sort_keys(O.KT_F32, I.normal_f32(3000, 2)).view(np.uint32))
+
+
 # ----------------------------------------------------------------- planted mistakes
 import oracle.ams_oracle as _M  # noqa: E402
 
@@ -584,6 +640,21 @@ def _bad_stable_partition(ids):                    # equal ids in reverse input 
     return len(ids) - 1 - np.argsort(ids[::-1], kind="stable")
 
 
+def _bad_count_before(q, key, i, pivot_seq, pivot_pos):  # sequence tie-break reversed
+    if i < pivot_seq:
+        return int(np.searchsorted(q, key, side="left"))
+    if i > pivot_seq:
+        return int(np.searchsorted(q, key, side="right"))
+    return pivot_pos
+
+
+def _bad_msel_definition(seqs, k):                 # ties not broken by sequence index
+    keys = np.concatenate([np.asarray(q, dtype=np.uint64) for q in seqs])
+    sid = np.concatenate([np.full(len(q), i, dtype=np.int64) for i, q in enumerate(seqs)])
+    order = np.argsort(keys, kind="quicksort")
+    return [int(np.sum(sid[order[:k]] == i)) for i in range(len(seqs))]
+
+
 def _bad_a_for(self, n_g, nbuckets):               # sample-size cap dropped
     return self.a if self.a else _M.oversampling_factor(n_g)
 
@@ -608,6 +679,9 @@ PLANTED = [
     ("partition not stable", "stable_partition", _bad_stable_partition, "test_ams_restatement_equals_definition",
      {"dist": "zipf"}),
     ("a without its cap", "Plan.a_for", _bad_a_for, "test_a_for_hand_values", {}),
+    ("multiselect tie-break reversed", "_count_before", _bad_count_before, "test_multiseq_select_hand_example", {}),
+    ("multiselect ties unbroken", "multiseq_select_definition", _bad_msel_definition,
+     "test_multiseq_select_brute_force", {}),
 ]
 
 
@@ -621,7 +695,8 @@ def test_pins_catch_planted_mistakes(monkeypatch, what, attr, bad, pin, kw):
         monkeypatch.setattr(_M.Plan, attr.split(".")[1], bad)
     else:
         monkeypatch.setattr(_M, attr, bad)
-        monkeypatch.setattr(O, attr, bad)
+        if hasattr(O, attr):  # (private helpers are not re-exported)
+            monkeypatch.setattr(O, attr, bad)
     with pytest.raises(AssertionError):
         pin_fn(**kw)
 
