@@ -369,6 +369,31 @@ def run_segmented_sub(reps=3):
             "plan": f"levels {wl['levels']}, r {wl['buckets']}, b {wl['b']}; segments <= C go to the base case"}
 
 
+def run_rlm_sub(peak, reps=3):
+    """RLM-sort (Section 5) of the same 2^28 uniform uint64 keys: tiles of 8192 keys,
+    parts 256 x 128 (so that the last level's parts are single tiles), out of place,
+    output checked.  Algorithmic bytes: (levels x 2 + 1) passes of read + write (the
+    tile sorts of every level and every delivery)."""
+    import torch
+
+    import paper_1410_6754_gb300 as ams
+    from paper_1410_6754_gb300 import inputs as I
+    n, run, parts = 1 << 28, 8192, [256, 128]
+    src = I.generate("uniform", n, 0, 64, device="cuda")
+    dst = torch.empty_like(src)
+    ctx = ams.Context()
+    ms = _timed(lambda: ams.rlm_sort(src, dst, run=run, parts=parts, seed=0, kt=1, ctx=ctx), reps)
+    ctx.sync()
+    ok = _check_sorted(src, dst, 64)
+    ctx.close()
+    del src, dst
+    torch.cuda.empty_cache()
+    alg = (2 * len(parts) + 1) * 2 * n * 8
+    return {"n": n, "run": run, "parts": parts, "ms": ms, "keys_per_s": n / (ms * 1e-3), "ok": ok,
+            "step_roofline_frac": alg / (ms * 1e-3) / 1e9 / peak,
+            "definition": "(2 x levels + 1) x (read + write) x n x key bytes"}
+
+
 def serving_bench(n_requests, streams, tuned, seed=5):
     """Serving loop: a seeded Poisson stream of mixed requests (sizes log-uniform in
     [2^10, 2^26]; key types 50% uint32 / 30% uint64 / 20% float32; uniform or Zipf
@@ -651,6 +676,7 @@ def run_ams(args, wl):
         t_ex = time.perf_counter()
         extras["configs"] = run_configs(peak)
         extras["segmented"] = run_segmented_sub()
+        extras["rlm"] = run_rlm_sub(peak)
         extras["serving"] = serving_bench(args.requests, args.server_streams, args.tuned)
         extras["extras_wall_s"] = time.perf_counter() - t_ex
 
@@ -711,7 +737,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ams", choices=["ams", "reference"])
     ap.add_argument("--workload", default="two_level_u64", choices=sorted(WORKLOADS) + ["serving"])
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--requests", type=int, default=400, help="serving: request count")
     ap.add_argument("--no-extras", action="store_true",

@@ -75,6 +75,17 @@ typedef struct ams_options {
 #define AMS_FLAG_TREE_CLASSIFIER 0x2u  /* classify by descending the implicit splitter
                                           tree (Section 2.2 multisplitter) instead of the
                                           default cell table; same bucket ids */
+#define AMS_FLAG_GRAPH 0x4u  /* keys-only sorts of one array (n >= 2): replay a CUDA
+                                graph per size class instead of launching every kernel.
+                                The context pads the request to its class size (the next
+                                power of two, at least 1024) with keys that order after
+                                every key, captures the class's launch sequence once on
+                                buffers of its own, and per call only updates the copy
+                                in, the pad fill and the copy out.  Same result; the
+                                context keeps 2 x class size keys per class in use, and
+                                a graph is rebuilt when its scratch had to move.  The
+                                first call of a class captures (no stream may be
+                                capturing then). */
 
 /* --------------------------------------------------------------- whole sorts */
 

@@ -24,6 +24,7 @@ U32, U64, F32 = 0, 1, 2
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_INTERNAL = range(7)
 FLAG_PHASE_TIMERS = 1
 FLAG_TREE_CLASSIFIER = 2
+FLAG_GRAPH = 4
 KERNEL_KINDS = ("init", "setup", "sample_sort", "cross_rank", "splitters", "classify", "scan",
                 "binpack", "scatter", "basecase", "table")
 

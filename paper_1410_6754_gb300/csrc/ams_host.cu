@@ -203,6 +203,21 @@ struct Context {
   // step calls
   char* step_ws = nullptr;
   size_t step_bytes = 0;
+  // graphs per size class (AMS_FLAG_GRAPH)
+  struct GraphEntry {
+    int kt = 0, levels = 0;
+    uint32_t r[kMaxLevels] = {}, a = 0, b = 0, cap = 0, flags = 0;
+    uint64_t seed = 0, n_class = 0, ws_gen = 0;
+    char* buf = nullptr;  // input then output, n_class keys each
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t copy_in = nullptr, pad = nullptr, copy_out = nullptr;
+    uint32_t launches = 0;  // kernels of the captured sort
+  };
+  std::vector<GraphEntry> graphs;
+  size_t graph_bytes = 0;
+  uint64_t ws_gen = 0;  // bumped whenever the workspace moves (captured graphs then stale)
+  cudaStream_t cap_stream = nullptr;
   // RLM-sort tables (pinned staging; the event marks the end of the last copy)
   void* rlm_host = nullptr;
   size_t rlm_host_bytes = 0;
@@ -226,7 +241,7 @@ static ams_status cuda_status(cudaError_t e) {
 
 static ams_status grow(Context* cx, char** buf, size_t* have, size_t need) {
   if (*have >= need) return AMS_OK;
-  const size_t total = cx->ws_bytes + cx->stage_bytes + cx->step_bytes - *have + need;
+  const size_t total = cx->ws_bytes + cx->stage_bytes + cx->step_bytes + cx->graph_bytes - *have + need;
   if (cx->budget && total > cx->budget) return AMS_ERR_OOM;
   if (*buf) {
     cudaError_t e = cudaDeviceSynchronize();
@@ -251,6 +266,7 @@ static ams_status ensure_ws(Context* cx, size_t need) {
   ams_status st = grow(cx, &cx->ws, &cx->ws_bytes, need);
   if (st != AMS_OK) return st;
   if (fresh) {
+    ++cx->ws_gen;
     cx->d_status = (uint32_t*)cx->ws;
     AMS_TRY(cudaMemset(cx->d_status, 0, 256));
   }
@@ -307,6 +323,8 @@ static void fill_thr(double* thr) {
 }
 
 // --------------------------------------------------------------- one whole sort
+static ams_status run_sort_graph(Context* cx, const ams_request* rq, cudaStream_t s);
+
 static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
   if (!rq) return AMS_ERR_INVALID;
   const bool pairs = rq->vals_in != nullptr || rq->vals_out != nullptr;
@@ -317,6 +335,9 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
   if (!rq->keys_in || !rq->keys_out) return AMS_ERR_INVALID;
   const int ks = ksize_of(rq->kt);
   if (((uintptr_t)rq->keys_in % ks) || ((uintptr_t)rq->keys_out % ks)) return AMS_ERR_INVALID;
+  if ((rq->opt.flags & AMS_FLAG_GRAPH) && !pairs && !rq->d_offsets && rq->n >= 2 &&
+      !(rq->opt.flags & AMS_FLAG_PHASE_TIMERS))
+    return run_sort_graph(cx, rq, s);
   Plan p;
   ams_status st = make_plan(rq->n, nseg_user, rq->kt, pairs, rq->levels, rq->buckets_per_level,
                             &rq->opt, cx->sm_count, &p);
@@ -486,6 +507,145 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
     if (la.last && (st = run_basecase(la.dst, la.vdst, b.big, &b.ctr[l].n_big, 0, p.big_cap, true)) != AMS_OK)
       return st;
   }
+  return AMS_OK;
+}
+
+// ---------------------------------------------------------------- graphs per class
+// Keys at or after the last position of a padded request: the largest key of the
+// type in order form, stored as its bit pattern (f32: 0x7FFFFFFF, whose order map is
+// the largest 32-bit value).
+__global__ void k_fill_pad(void* p, uint64_t count, int ksize, uint64_t pattern) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
+    if (ksize == 8) ((uint64_t*)p)[i] = pattern;
+    else ((uint32_t*)p)[i] = (uint32_t)pattern;
+  }
+}
+
+static bool same_plan(const Context::GraphEntry& g, const ams_request* rq, uint64_t n_class) {
+  if (g.kt != (int)rq->kt || g.levels != rq->levels || g.n_class != n_class || g.seed != rq->seed) return false;
+  for (int l = 0; l < rq->levels; ++l)
+    if (g.r[l] != rq->buckets_per_level[l]) return false;
+  return g.a == rq->opt.oversample_a && g.b == rq->opt.overpartition_b && g.cap == rq->opt.basecase_cap &&
+         g.flags == (rq->opt.flags & ~AMS_FLAG_GRAPH);
+}
+
+static void pad_params(cudaKernelNodeParams& kp, void** args, void*& ptr, uint64_t& cnt, int& ks, uint64_t& pat,
+                       int grid) {
+  kp = cudaKernelNodeParams{};
+  kp.func = (void*)k_fill_pad;
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(256);
+  args[0] = &ptr;
+  args[1] = &cnt;
+  args[2] = &ks;
+  args[3] = &pat;
+  kp.kernelParams = args;
+}
+
+static ams_status run_sort_graph(Context* cx, const ams_request* rq, cudaStream_t s) {
+  const int ks = ksize_of(rq->kt);
+  uint64_t n_class = 1024;
+  while (n_class < rq->n) n_class <<= 1;
+  if (n_class >= 0xFFFFFFFFull) return AMS_ERR_UNSUPPORTED;
+  const uint64_t pattern = rq->kt == AMS_F32 ? 0x7FFFFFFFull : ~0ull;
+  Context::GraphEntry* ge = nullptr;
+  for (auto& g : cx->graphs)
+    if (same_plan(g, rq, n_class)) ge = &g;
+  if (ge && ge->ws_gen != cx->ws_gen) {  // its workspace moved: capture again
+    cudaGraphExecDestroy(ge->exec);
+    cudaGraphDestroy(ge->graph);
+    ge->exec = nullptr;
+    ge->graph = nullptr;
+  }
+  int pgrid = 64;
+  void* pad_ptr = nullptr;
+  uint64_t pad_cnt = 0;
+  int pad_ks = ks;
+  uint64_t pad_pat = pattern;
+  void* pargs[4];
+  cudaKernelNodeParams kp;
+  if (!ge || !ge->exec) {
+    if (!ge) {
+      cx->graphs.emplace_back();
+      ge = &cx->graphs.back();
+      ge->kt = (int)rq->kt;
+      ge->levels = rq->levels;
+      for (int l = 0; l < rq->levels; ++l) ge->r[l] = rq->buckets_per_level[l];
+      ge->a = rq->opt.oversample_a;
+      ge->b = rq->opt.overpartition_b;
+      ge->cap = rq->opt.basecase_cap;
+      ge->flags = rq->opt.flags & ~AMS_FLAG_GRAPH;
+      ge->seed = rq->seed;
+      ge->n_class = n_class;
+      const size_t bytes = 2 * (size_t)n_class * ks;
+      if (cx->budget && cx->ws_bytes + cx->stage_bytes + cx->step_bytes + cx->graph_bytes + bytes > cx->budget)
+        return AMS_ERR_OOM;
+      if (cudaMalloc(&ge->buf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cx->graphs.pop_back();
+        return AMS_ERR_OOM;
+      }
+      cx->graph_bytes += bytes;
+    }
+    char* in = ge->buf;
+    char* out = ge->buf + (size_t)n_class * ks;
+    // the sort of the class size on the entry's buffers, captured on a stream of the
+    // context's own (the workspace is sized first: nothing allocates during capture)
+    ams_request inner = *rq;
+    inner.keys_in = in;
+    inner.keys_out = out;
+    inner.n = n_class;
+    inner.opt.flags &= ~(AMS_FLAG_GRAPH | AMS_FLAG_PHASE_TIMERS);
+    const uint64_t need = ams_request_scratch_bytes(&inner);
+    if (need == 0) return AMS_ERR_INVALID;
+    ams_status st = ensure_ws(cx, need);
+    if (st != AMS_OK) return st;
+    if (!cx->cap_stream) AMS_TRY(cudaStreamCreateWithFlags(&cx->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t sort_graph = nullptr;
+    const uint32_t l0 = cx->launches;
+    AMS_TRY(cudaStreamBeginCapture(cx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    st = run_sort(cx, &inner, cx->cap_stream);
+    const cudaError_t ce = cudaStreamEndCapture(cx->cap_stream, &sort_graph);
+    if (st != AMS_OK || ce != cudaSuccess) {
+      if (sort_graph) cudaGraphDestroy(sort_graph);
+      cudaGetLastError();
+      return st != AMS_OK ? st : AMS_ERR_CUDA;
+    }
+    ge->launches = cx->launches - l0;
+    cx->launches = l0;
+    ge->ws_gen = cx->ws_gen;
+    // copy in -> pad fill -> the sort -> copy out
+    cudaGraph_t g = nullptr;
+    AMS_TRY(cudaGraphCreate(&g, 0));
+    ge->graph = g;
+    cudaGraphNode_t sort_node;
+    AMS_TRY(cudaGraphAddMemcpyNode1D(&ge->copy_in, g, nullptr, 0, in, rq->keys_in, rq->n * ks,
+                                     cudaMemcpyDeviceToDevice));
+    pad_ptr = in + rq->n * ks;
+    pad_cnt = n_class - rq->n;
+    pad_params(kp, pargs, pad_ptr, pad_cnt, pad_ks, pad_pat, pgrid);
+    AMS_TRY(cudaGraphAddKernelNode(&ge->pad, g, nullptr, 0, &kp));
+    cudaGraphNode_t deps[2] = {ge->copy_in, ge->pad};
+    AMS_TRY(cudaGraphAddChildGraphNode(&sort_node, g, deps, 2, sort_graph));
+    cudaGraphDestroy(sort_graph);  // (the child node holds a copy)
+    AMS_TRY(cudaGraphAddMemcpyNode1D(&ge->copy_out, g, &sort_node, 1, rq->keys_out, out, rq->n * ks,
+                                     cudaMemcpyDeviceToDevice));
+    AMS_TRY(cudaGraphInstantiate(&ge->exec, g, 0));
+  } else {
+    char* in = ge->buf;
+    char* out = ge->buf + (size_t)n_class * ks;
+    AMS_TRY(cudaGraphExecMemcpyNodeSetParams1D(ge->exec, ge->copy_in, in, rq->keys_in, rq->n * ks,
+                                               cudaMemcpyDeviceToDevice));
+    pad_ptr = in + rq->n * ks;
+    pad_cnt = n_class - rq->n;
+    pad_params(kp, pargs, pad_ptr, pad_cnt, pad_ks, pad_pat, pgrid);
+    AMS_TRY(cudaGraphExecKernelNodeSetParams(ge->exec, ge->pad, &kp));
+    AMS_TRY(cudaGraphExecMemcpyNodeSetParams1D(ge->exec, ge->copy_out, rq->keys_out, out, rq->n * ks,
+                                               cudaMemcpyDeviceToDevice));
+  }
+  AMS_TRY(cudaGraphLaunch(ge->exec, s));
+  cx->launches += ge->launches + 1;  // the sort's kernels and the pad fill
+  cx->last_stream = s;
   return AMS_OK;
 }
 
@@ -760,6 +920,12 @@ ams_status ams_context_destroy(void* ctx) {
     cudaEventDestroy(cx->rlm_done);
   }
   if (cx->rlm_host) cudaFreeHost(cx->rlm_host);
+  for (auto& g : cx->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    if (g.buf) cudaFree(g.buf);
+  }
+  if (cx->cap_stream) cudaStreamDestroy(cx->cap_stream);
   delete cx;
   return AMS_OK;
 }
@@ -803,7 +969,7 @@ ams_status ams_context_reserve(void* ctx, uint64_t bytes) {
 
 uint64_t ams_context_scratch_bytes(void* ctx) {
   Context* cx = ctx_or_default(ctx);
-  return cx ? (uint64_t)(cx->ws_bytes + cx->stage_bytes + cx->step_bytes) : 0;
+  return cx ? (uint64_t)(cx->ws_bytes + cx->stage_bytes + cx->step_bytes + cx->graph_bytes) : 0;
 }
 
 ams_status ams_get_stats(void* ctx, ams_stats* out) {
