@@ -406,10 +406,13 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
     cudaError_t e = ln.end(launch_basecase(ba, p.ksize, p.pairs, big, grid, s));
     return cuda_status(e);
   };
-  if ((st = run_basecase(rq->keys_in, rq->vals_in, b.bc0, &b.ctr[0].n_bc, f32 ? 1 : 0, p.bc0_cap,
-                         false)) != AMS_OK)
+  // no offsets and n above C: one segment [0, n) that level 0 hands to level 1, so
+  // there is no base-case item and no tiny segment
+  const bool one_big = rq->d_offsets == nullptr && rq->n > p.C;
+  if (!one_big && (st = run_basecase(rq->keys_in, rq->vals_in, b.bc0, &b.ctr[0].n_bc, f32 ? 1 : 0,
+                                     p.bc0_cap, false)) != AMS_OK)
     return st;
-  {
+  if (!one_big) {
     // user segments of at most kTiny keys: one warp each (all-pairs ranks)
     BaseArgs ta = ba;
     ta.src = rq->keys_in;
@@ -497,7 +500,7 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
     ln.begin(AMS_K_CLASSIFY);
     AMS_TRY(ln.end(launch_classify(la, p.ksize, tree, SM * 6, s)));
     ln.begin(AMS_K_SCAN);
-    AMS_TRY(ln.end(launch_scan(la, SM * 8, s)));
+    AMS_TRY(ln.end(launch_scan(la, SM * 8, lp.nseg_cap <= 16, s)));
     ln.begin(AMS_K_BINPACK);
     AMS_TRY(ln.end(launch_binpack(la, seg_grid, s)));
     ln.begin(AMS_K_SCATTER);
@@ -1357,7 +1360,7 @@ ams_status ams_step_classify(const void* d_keys, uint64_t n, ams_key_type kt, co
   AMS_TRY(launch_table(la, ks, 1, s));
   if (d_ids) la.ids = d_ids;
   AMS_TRY(launch_classify(la, ks, false, cx->sm_count * 4, s));
-  AMS_TRY(launch_scan(la, cx->sm_count * 8, s));
+  AMS_TRY(launch_scan(la, cx->sm_count * 8, true, s));
   AMS_TRY(cudaMemcpyAsync(d_counts, w.totals, (size_t)la.nid * 4, cudaMemcpyDeviceToDevice, s));
   return AMS_OK;
 }
@@ -1415,7 +1418,7 @@ ams_status ams_step_partition(const void* d_in, void* d_out, const uint64_t* d_v
   la.pieces_per_id = 1;  // deliver bucket by bucket
   AMS_TRY(launch_table(la, ks, 1, s));
   AMS_TRY(launch_classify(la, ks, false, cx->sm_count * 4, s));
-  AMS_TRY(launch_scan(la, cx->sm_count * 8, s));
+  AMS_TRY(launch_scan(la, cx->sm_count * 8, true, s));
   AMS_TRY(launch_binpack(la, 1, s));
   AMS_TRY(launch_scatter(la, ks, d_vals_in != nullptr, /*stable=*/true, cx->sm_count * 2, s));
   return AMS_OK;

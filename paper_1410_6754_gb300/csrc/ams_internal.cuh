@@ -213,7 +213,7 @@ cudaError_t launch_cross_rank(const LevelArgs& a, int ksize, int grid, cudaStrea
 cudaError_t launch_splitters(const LevelArgs& a, int ksize, int grid, cudaStream_t s);
 cudaError_t launch_table(const LevelArgs& a, int ksize, int grid, cudaStream_t s);
 cudaError_t launch_classify(const LevelArgs& a, int ksize, bool tree, int grid, cudaStream_t s);
-cudaError_t launch_scan(const LevelArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_scan(const LevelArgs& a, int grid, bool few_segments, cudaStream_t s);
 cudaError_t launch_binpack(const LevelArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_scatter(const LevelArgs& a, int ksize, bool pairs, bool stable, int grid,
                            cudaStream_t s);

@@ -323,24 +323,16 @@ __device__ __forceinline__ void sort_loaded(K (&x)[BaseCfg<K, PAIRS>::KPT], K* d
   // at its final place; the second arrival of a cell lists the cell for sorting.
 #pragma unroll
   for (int q = 0; q < KPT; ++q) {
-    if ((uint32_t)q * NT >= m) break;  // (uniform)
+    if ((uint32_t)q * NT >= m) break;
     const uint32_t e = tid + q * NT;
-    uint32_t c = 0, r = 0;
     if (e < m) {
-      c = cell(x[q]);
-      r = (rr[q >> 1] >> ((q & 1) << 4)) & 0xFFFFu;
+      const uint32_t c = cell(x[q]);
+      const uint32_t r = (rr[q >> 1] >> ((q & 1) << 4)) & 0xFFFFu;
       const uint32_t s = c16[c] + r;
       sm.keys[s] = x[q];
       if constexpr (PAIRS) sm.pos[s] = (uint16_t)e;
-    }
-    // the warp's second arrivals reserve their list entries with one atomic
-    const uint32_t second = __ballot_sync(0xFFFFFFFFu, e < m && r == 1);
-    if (second) {
-      uint32_t base = 0;
-      if (lane == (uint32_t)(__ffs(second) - 1)) base = atomicAdd(&sm.flag[2], (uint32_t)__popc(second));
-      base = __shfl_sync(0xFFFFFFFFu, base, __ffs(second) - 1);
-      if (e < m && r == 1) {
-        const uint32_t i = base + __popc(second & lanemask_lt());
+      if (r == 1) {
+        const uint32_t i = atomicAdd(&sm.flag[2], 1u);
         if (i < C::LIST) sm.shared[i] = (uint16_t)c;
       }
     }

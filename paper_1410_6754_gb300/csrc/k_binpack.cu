@@ -5,12 +5,14 @@
 //   * exclusive scan of the 2B-1 bucket sizes -> bucket starts (relative to the
 //     segment), overwriting the totals table;
 //   * the optimal bound L* of the scanning algorithm over the range-bucket sizes
-//     (equality buckets weigh 0: they are final).  Search of Appendix C: each round
-//     16 warps scan 16 bounds spread over [lo, hi); a successful scan lowers hi to
-//     the largest group it formed, a failed one raises lo to the smallest
-//     "group + next bucket" load it saw; the answer is lo == hi.  One warp scans
-//     one bound: a group starting at bucket s ends at the largest e with
-//     P[e] - P[s] <= L, found 32 buckets at a time by a ballot;
+//     (equality buckets weigh 0: they are final).  Binary search on L with the two
+//     roundings of Appendix C: a successful scan lowers hi to the largest group it
+//     formed, a failed one raises lo to the smallest "group + next bucket" load it
+//     saw; the answer is lo == hi.  One scan at bound L runs on the whole block: the
+//     end of the group starting at every bucket s (the largest e with
+//     P[e] - P[s] <= L, by binary search over the prefix sums P), then pointer
+//     doubling over those ends, so that the end of group k is a composition of
+//     log2(r) tables -- O(log B + log r) dependent steps instead of r;
 //   * the groups at L*, then the pieces of every group (one thread per group):
 //     equality buckets holding at least max(2, L*/16) keys become final pieces,
 //     the rest of the group stays one piece; pieces larger than C go to the next
@@ -22,57 +24,85 @@
 
 namespace ams {
 
-constexpr uint32_t kKeepR = 256;  // largest r whose per-warp group ends stay in shared memory
-constexpr int kCand = 16;          // bounds tried per search round (one warp each)
-
-struct ScanResult {
-  uint32_t groups;  // groups formed (stops counting past r)
-  uint32_t used;    // largest group formed
-  uint64_t zmin;    // smallest (group + next bucket) seen when closing a group
+// Tables of one scan at bound L.  T[j][i] (j < nlev, i <= B) = the bucket where the
+// 2^j groups formed from bucket i end (B: the end); ends[k] = end of group k from
+// bucket 0 (B once the buckets are used up).
+struct ScanTables {
+  uint16_t* T;    // nlev rows of B + 1 entries
+  uint32_t nlev;  // floor(log2 r) + 1
+  uint32_t* ends;
 };
 
-// Scanning algorithm with bound L over prefix sums P[0..B] (P[0] = 0), by one warp.
-// A group starting at bucket s ends at the largest e with P[e] - P[s] <= L: lane l
-// holds P[s+1+l], a ballot counts the buckets that fit (they form a prefix of the
-// lanes), and the group's load and the next bucket's prefix come from the same
-// registers -- one shared-memory load per group on the dependent chain.
-__device__ ScanResult warp_scan_groups(const uint32_t* P, uint32_t B, uint32_t r, uint32_t L,
-                                       uint32_t* ends) {
-  const uint32_t lane = threadIdx.x & 31;
-  ScanResult res{0, 0, ~0ull};
-  uint32_t s = 0, base = P[0];
-  uint32_t win = 1 + lane <= B ? P[1 + lane] : 0u;
-  while (s < B) {
-    if (res.groups == r) {  // one group too many: infeasible
-      res.groups = r + 1;
-      break;
-    }
-    ++res.groups;
-    const uint32_t m = __ballot_sync(0xFFFFFFFFu, s + 1 + lane <= B && win - base <= L);
-    uint32_t c = __popc(m);  // >= 1: every bucket fits alone
-    uint32_t pe;             // P[s + c]
-    if (c < 32) {
-      pe = __shfl_sync(0xFFFFFFFFu, win, c - 1);
-    } else {  // a group of more than 32 buckets
-      for (uint32_t off = s + 33;; off += 32) {
-        const uint32_t e = off + lane;
-        const uint32_t cc = __popc(__ballot_sync(0xFFFFFFFFu, e <= B && P[e] - base <= L));
-        c += cc;
-        if (cc < 32) break;
+struct ScanResult {
+  uint32_t feasible;  // r groups cover every bucket
+  uint32_t groups;    // groups formed (at most r)
+  uint32_t used;      // largest group formed
+  uint32_t zmin;      // smallest (group + next bucket) seen when closing a group (~0u: none)
+};
+
+// Scanning algorithm with bound L >= the largest bucket over prefix sums P[0..B]
+// (P[0] = 0), by the whole block of NT threads; ends with a barrier.
+template <int NT>
+__device__ ScanResult block_scan_groups(const uint32_t* P, uint32_t B, uint32_t r, uint32_t L,
+                                        const ScanTables& t, uint32_t* red) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const uint32_t row = B + 1;
+  // the group starting at bucket i ends at the largest e in [i+1, B] with
+  // P[e] - P[i] <= L (bucket i alone always fits)
+  for (uint32_t i = tid; i <= B; i += NT) {
+    uint32_t lo = i + 1, hi = B;
+    if (i < B) {
+      const uint32_t base = P[i];
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (P[mid] - base <= L) lo = mid; else hi = mid - 1;
       }
-      pe = P[s + c];
     }
-    const uint32_t e = s + c;
-    res.used = max(res.used, pe - base);
-    if (e < B) {
-      const uint32_t pn = c < 32 ? __shfl_sync(0xFFFFFFFFu, win, c) : P[e + 1];
-      res.zmin = min(res.zmin, (uint64_t)(pn - base));
-    }
-    if (ends && lane == 0) ends[res.groups - 1] = e;
-    s = e;
-    base = pe;
-    win = s + 1 + lane <= B ? P[s + 1 + lane] : 0u;
+    t.T[i] = (uint16_t)(i < B ? lo : B);
   }
+  __syncthreads();
+  for (uint32_t j = 1; j < t.nlev; ++j) {
+    const uint16_t* src = t.T + (j - 1) * row;
+    uint16_t* dst = t.T + j * row;
+    for (uint32_t i = tid; i <= B; i += NT) dst[i] = src[src[i]];
+    __syncthreads();
+  }
+  // group k ends after k + 1 groups from bucket 0; its load and closing value
+  uint32_t used = 0, zmin = ~0u, formed = 0;
+  for (uint32_t k = tid; k < r; k += NT) {
+    uint32_t e = 0, s = 0;
+    for (uint32_t j = 0, v = k + 1; v; ++j, v >>= 1)
+      if (v & 1) e = t.T[j * row + e];
+    if (k) {
+      s = 0;
+      for (uint32_t j = 0, v = k; v; ++j, v >>= 1)
+        if (v & 1) s = t.T[j * row + s];
+    }
+    t.ends[k] = e;
+    if (s < B) {
+      ++formed;
+      used = max(used, P[e] - P[s]);
+      if (e < B) zmin = min(zmin, P[e + 1] - P[s]);
+    }
+  }
+  used = __reduce_max_sync(0xFFFFFFFFu, used);
+  zmin = __reduce_min_sync(0xFFFFFFFFu, zmin);
+  formed = __reduce_add_sync(0xFFFFFFFFu, formed);
+  constexpr int NW = NT / 32;
+  if (lane == 0) {
+    red[w] = used;
+    red[NW + w] = zmin;
+    red[2 * NW + w] = formed;
+  }
+  __syncthreads();
+  ScanResult res{0, 0, 0, ~0u};
+  for (int i = 0; i < NW; ++i) {
+    res.used = max(res.used, red[i]);
+    res.zmin = min(res.zmin, red[NW + i]);
+    res.groups += red[2 * NW + i];
+  }
+  res.feasible = t.ends[r - 1] == B;
+  __syncthreads();  // (red and the tables are rewritten by the next scan)
   return res;
 }
 
@@ -159,14 +189,13 @@ __global__ void __launch_bounds__(512, 2) k_binpack(LevelArgs a) {
   uint32_t* bst_s = cnt_s + nid;       // nid + 1
   uint32_t* P = bst_s + nid + 1;       // B + 1
   uint32_t* ends = P + B + 1;          // r
+  uint32_t* pc_s = ends + a.r;         // r (piece counts of the groups)
+  const ScanTables tab{(uint16_t*)(pc_s + a.r), 32u - (uint32_t)__clz((int)a.r), ends};
   __shared__ uint32_t ws[33];
-  __shared__ unsigned long long lohi[2];
-  __shared__ ScanResult wres[32];
-  __shared__ uint32_t ngroups_s, best_s;
+  __shared__ uint32_t red[3 * (NT / 32)];
   __shared__ uint32_t base_s[3];
-  __shared__ int best_w;
   const uint32_t nseg = a.ctr->nseg;
-  const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const uint32_t tid = threadIdx.x;
 
   for (uint32_t g = blockIdx.x; g < nseg; g += gridDim.x) {
     const Seg sg = a.segs[g];
@@ -183,79 +212,30 @@ __global__ void __launch_bounds__(512, 2) k_binpack(LevelArgs a) {
     for (uint32_t j = tid; j < B; j += NT) mw = max(mw, P[j]);
     const uint32_t max_w = block_reduce_max<NT, uint32_t>(mw, ws);
     const uint32_t W = block_scan_array<NT, uint32_t>(P, B, ws);
-    if (tid == 0) {
-      P[B] = W;
-      const uint64_t lo = max((uint64_t)((W + (uint64_t)a.r - 1) / a.r), (uint64_t)max_w);
-      lohi[0] = lo;
-      lohi[1] = min((uint64_t)W, lo + max_w);
-    }
+    if (tid == 0) P[B] = W;
     __syncthreads();
-    // optimal bound (Section 6 Lemma; Appendix C search).  Every round moves lo up
-    // or hi down; 64 rounds cannot be exhausted on valid input (the range starts
-    // below 2^32 and shrinks at least kCand-fold per round).  The cap only guards
-    // against a logic error: it keeps the feasible hi and flags the status word.
-    // A successful scan at bound c whose largest group is u forms the same groups as
-    // the scan at bound u; so the groups of the scan that set hi last are the groups
-    // at L* when the search ends on that hi (kept when r <= kKeepR, else rescanned).
-    const bool keep = a.r <= kKeepR;
-    uint32_t* wends = ends + a.r;  // kCand slots of r group ends
-    if (tid == 0) best_s = 0xFFFFFFFFu;
-    for (int round = 0;; ++round) {
-      const uint64_t lo = lohi[0], hi = lohi[1];
-      if (lo >= hi) break;
-      if (round == 64) {
-        __syncthreads();
-        if (tid == 0) {
-          lohi[0] = hi;
-          best_s = 0xFFFFFFFFu;
-          atomicOr(a.status, ST_OVERFLOW);
-        }
-        __syncthreads();
+    // optimal bound (Section 6 Lemma; Appendix C search).  L* lies in [lo, hi]: no
+    // bound below max(ceil(W/r), largest bucket) can succeed, and W/r + the largest
+    // bucket always does.  Every step moves lo above the candidate or hi to at most
+    // it; 64 steps cannot be exhausted on valid input (the range starts below 2^32
+    // and halves at least).  The cap only guards against a logic error: it keeps the
+    // feasible hi and flags the status word.  (lo, hi: the same in every thread.)
+    uint64_t lo = max((uint64_t)((W + (uint64_t)a.r - 1) / a.r), (uint64_t)max_w);
+    uint64_t hi = min((uint64_t)W, lo + max_w);
+    for (int step = 0; lo < hi; ++step) {
+      if (step == 64) {
+        if (tid == 0) atomicOr(a.status, ST_OVERFLOW);
+        lo = hi;
         break;
       }
-      if (w < (uint32_t)kCand) {
-        const uint64_t cand = lo + (hi - lo) * w / kCand;
-        const ScanResult rs = warp_scan_groups(P, B, a.r, (uint32_t)cand, keep ? wends + w * a.r : nullptr);
-        if (lane == 0) wres[w] = rs;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        uint64_t nlo = lo, nhi = hi;
-        int kbest = -1;
-        for (int k = 0; k < kCand; ++k) {
-          if (wres[k].groups <= a.r) {
-            if ((uint64_t)wres[k].used < nhi) {
-              nhi = wres[k].used;
-              kbest = k;
-            }
-          } else {
-            nlo = max(nlo, wres[k].zmin);
-          }
-        }
-        lohi[0] = nlo;
-        lohi[1] = max(nlo, nhi);
-        best_w = kbest;
-      }
-      __syncthreads();
-      if (keep && best_w >= 0) {  // keep the groups of the new hi
-        const uint32_t ngk = wres[best_w].groups;
-        for (uint32_t i = tid; i < ngk; i += NT) ends[i] = wends[best_w * a.r + i];
-        if (tid == 0) {
-          best_s = (uint32_t)wres[best_w].used;
-          ngroups_s = ngk;
-        }
-      }
-      __syncthreads();
+      const uint64_t cand = lo + (hi - lo) / 2;
+      const ScanResult rs = block_scan_groups<NT>(P, B, a.r, (uint32_t)cand, tab, red);
+      if (rs.feasible) hi = rs.used;  // lo <= L* <= used <= cand
+      else lo = max(lo, (uint64_t)rs.zmin);  // cand < zmin <= L*
     }
-    const uint64_t Lstar = lohi[0];
-    if (!(keep && best_s == (uint32_t)Lstar)) {
-      if (w == 0) {
-        const ScanResult rs = warp_scan_groups(P, B, a.r, (uint32_t)Lstar, ends);
-        if (lane == 0) ngroups_s = rs.groups;
-      }
-    }
-    __syncthreads();
-    const uint32_t ng = ngroups_s;
+    const uint64_t Lstar = lo;
+    // the groups at L*
+    const uint32_t ng = block_scan_groups<NT>(P, B, a.r, (uint32_t)Lstar, tab, red).groups;
     if (tid == 0) {
       a.seg_L[g] = (uint32_t)Lstar;
       a.seg_ng[g] = ng;
@@ -275,7 +255,6 @@ __global__ void __launch_bounds__(512, 2) k_binpack(LevelArgs a) {
       }
       if (tid == 0) a.npieces[g] = nid;
     } else {
-      uint32_t* pc_s = ends + a.r;  // r counters after the group ends (over the scan slots)
       for (uint32_t k = tid; k < ng; k += NT) {
         const uint32_t gs = k ? ends[k - 1] : 0, ge = ends[k];
         const uint32_t id_lo = 2 * gs, id_hi = min(2 * ge, nid);
@@ -399,10 +378,11 @@ cudaError_t launch_init(const InitArgs& a, int grid, cudaStream_t s) {
 
 cudaError_t launch_binpack(const LevelArgs& a, int grid, cudaStream_t s) {
   // dynamic + static shared memory may pass 48 KB even when the dynamic part alone
-  // does not, so the limit is always raised to what the launch asks for
-  // counts, starts, prefix sums, group ends, and kCand per-warp slots of group ends
-  // (r <= kKeepR) or the per-group piece counters
-  const size_t sm = (size_t)(a.nid + a.nid + 1 + a.B + 1 + a.r + (a.r <= kKeepR ? kCand : 1) * a.r) * 4;
+  // does not, so the limit is always raised to what the launch asks for.
+  // counts, starts, prefix sums, group ends, piece counts, then the scan's doubling
+  // tables: floor(log2 r) + 1 rows of B + 1 16-bit bucket indices
+  const uint32_t nlev = 32u - (uint32_t)__builtin_clz(a.r);
+  const size_t sm = (size_t)(a.nid + a.nid + 1 + a.B + 1 + 2 * a.r) * 4 + (size_t)nlev * (a.B + 1) * 2;
   cudaError_t e = cudaFuncSetAttribute(k_binpack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k_binpack<<<grid, 512, sm, s>>>(a);

@@ -176,8 +176,10 @@ __global__ void __launch_bounds__(512) k_classify(LevelArgs a) {
 // One block per (segment, 32 consecutive ids): lane l owns id 32*blk + l and warp w
 // a contiguous range of the segment's chunks (coalesced rows of 32 counts); warp
 // sums, their exclusive prefix over the warps, then the running prefix per warp.
-__global__ void __launch_bounds__(256) k_scan(LevelArgs a) {
-  constexpr int NW = 8;
+// NW = 32 warps for levels with few segments (the running sums are latency chains of
+// chunks / NW loads), 8 otherwise.
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) k_scan(LevelArgs a) {
   __shared__ uint32_t wsum[NW][32];
   const uint32_t nseg = a.ctr->nseg;
   const uint32_t nid = a.nid;
@@ -256,8 +258,11 @@ cudaError_t launch_classify(const LevelArgs& a, int ksize, bool tree, int grid, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_scan(const LevelArgs& a, int grid, cudaStream_t s) {
-  k_scan<<<grid, 256, 0, s>>>(a);
+cudaError_t launch_scan(const LevelArgs& a, int grid, bool few_segments, cudaStream_t s) {
+  if (few_segments)
+    k_scan<32><<<grid, 1024, 0, s>>>(a);
+  else
+    k_scan<8><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
