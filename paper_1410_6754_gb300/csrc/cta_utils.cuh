@@ -12,6 +12,16 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+// Asks L2 to fetch global bytes [p, p + bytes), rounded inward to 16-byte
+// boundaries (so nothing outside the range is touched): one bulk prefetch, no
+// registers, no shared memory and nothing to wait for.
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+  const uintptr_t b = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+  const uintptr_t e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+  if (e > b)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b), "r"((uint32_t)(e - b)) : "memory");
+}
+
 // Exclusive scan of one value per thread over a block of NT threads.  `ws` needs
 // NT/32 + 1 words of shared memory.  Returns the prefix; `total` gets the sum.
 template <int NT, typename T>

@@ -157,6 +157,8 @@ __global__ void __launch_bounds__(512) k_classify(LevelArgs a) {
     constexpr uint32_t U = 4;
     uint32_t v = threadIdx.x;
     for (; v + (U - 1) * NT < nv; v += U * NT) {
+      if (threadIdx.x == 0 && v + 3 * U * NT < nv)  // the window two rounds ahead into L2
+        prefetch_l2(vp + v + 2 * U * NT, (size_t)min(U * NT, nv - (v + 2 * U * NT)) * 16);
       uint4 w[U];
 #pragma unroll
       for (uint32_t u = 0; u < U; ++u) w[u] = __ldcs(vp + v + u * NT);

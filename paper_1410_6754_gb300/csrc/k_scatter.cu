@@ -283,6 +283,11 @@ __global__ void __launch_bounds__(ScatterKeysCfg::NT, ScatterKeysCfg::MINB) k_sc
 
     for (uint32_t t0 = lo; t0 < hi; t0 += TILE) {
       const uint32_t tn = min((uint32_t)TILE, hi - t0);
+      if (tid == 0 && t0 + TILE < hi) {  // the next tile's keys and ids into L2
+        const uint32_t nn = min((uint32_t)TILE, hi - (t0 + TILE));
+        prefetch_l2(src + t0 + TILE, (size_t)nn * sizeof(K));
+        prefetch_l2(ids + t0 + TILE, (size_t)nn * 2);
+      }
       K x[R];
       uint32_t pk[R];  // piece << 16 | place among the tile's keys of the piece
 #pragma unroll
