@@ -214,15 +214,16 @@ struct ScatterKeysCfg {
 
 template <typename K>
 __host__ __device__ constexpr size_t scatter_keys_smem_layout(uint32_t B, size_t* off) {
-  // offsets: piece_of, cnt, tbase, dbase, stage_key, stage_dst, ws
+  // offsets: piece_of, cnt, (tile start, run offset) pairs, unused, stage_key, stage_dst, ws
   using C = ScatterKeysCfg;
   const uint32_t nid = 2 * B - 1;
   size_t o = 0;
   off[0] = o; o += (size_t)nid * 2;
   o = (o + 15) & ~(size_t)15;
   off[1] = o; o += (size_t)(nid + 1) * 4;
-  off[2] = o; o += (size_t)(nid + 1) * 4;
-  off[3] = o; o += (size_t)nid * 4;
+  o = (o + 15) & ~(size_t)15;
+  off[2] = o; o += (size_t)(nid + 1) * 8;
+  off[3] = o;
   o = (o + 15) & ~(size_t)15;
   off[4] = o; o += (size_t)C::TILE * sizeof(K);
   off[5] = o; o += (size_t)C::TILE * 4;
@@ -239,9 +240,10 @@ __global__ void __launch_bounds__(ScatterKeysCfg::NT, ScatterKeysCfg::MINB) k_sc
   scatter_keys_smem_layout<K>(a.B, off);
   const uint32_t nid = a.nid;
   uint16_t* piece_of = (uint16_t*)(smem + off[0]);
-  uint32_t* cnt = (uint32_t*)(smem + off[1]);    // keys of each piece in the tile
-  uint32_t* tbase = (uint32_t*)(smem + off[2]);  // tile start of each piece; [P] = tile size
-  uint32_t* dbase = (uint32_t*)(smem + off[3]);  // run offset of each piece
+  uint32_t* cnt = (uint32_t*)(smem + off[1]);  // keys of each piece in the tile
+  // per piece: x = its start in the tile ([P].x = tile size), y = its run offset
+  // (one 64-bit load gives both when a key is staged)
+  uint2* td = (uint2*)(smem + off[2]);
   K* stage_key = (K*)(smem + off[4]);
   uint32_t* stage_dst = (uint32_t*)(smem + off[5]);
   uint32_t* ws = (uint32_t*)(smem + off[6]);
@@ -268,14 +270,14 @@ __global__ void __launch_bounds__(ScatterKeysCfg::NT, ScatterKeysCfg::MINB) k_sc
     }
     const uint32_t* pst = a.piece_start + (size_t)g * nid;
     for (uint32_t p = tid; p < P; p += NT) {
-      dbase[p] = sg.begin + pst[p];
+      td[p].y = sg.begin + pst[p];
       cnt[p] = 0;
     }
     __syncthreads();
     const uint32_t* coff = a.counts + (size_t)k * nid;
     for (uint32_t i = tid; i < nid; i += NT) {
       const uint32_t c = coff[i];
-      if (c) atomicAdd(&dbase[piece_of[i]], c);
+      if (c) atomicAdd(&td[piece_of[i]].y, c);
     }
     const uint32_t lo = sg.begin + (k - si.item_off) * a.CH;
     const uint32_t hi = (uint32_t)min((uint64_t)lo + a.CH, (uint64_t)sg.end);
@@ -322,7 +324,7 @@ __global__ void __launch_bounds__(ScatterKeysCfg::NT, ScatterKeysCfg::MINB) k_sc
         }
       }
       __syncthreads();  // (1)
-      // exclusive scan of cnt[0..P) into tbase, each thread a run of `ch` pieces;
+      // exclusive scan of cnt[0..P) into td[].x, each thread a run of `ch` pieces;
       // the counts are cleared for the next tile on the way
       const uint32_t ch = (P + NT - 1) / NT;
       const uint32_t cb = min(tid * ch, P), ce = min(cb + ch, P);
@@ -341,11 +343,11 @@ __global__ void __launch_bounds__(ScatterKeysCfg::NT, ScatterKeysCfg::MINB) k_sc
       for (int j = 0; j < NW; ++j) run += j < (int)w ? ws[j] : 0u;
       for (uint32_t i = cb; i < ce; ++i) {
         const uint32_t c = cnt[i];
-        tbase[i] = run;
+        td[i].x = run;
         run += c;
         cnt[i] = 0;
       }
-      if (tid == 0) tbase[P] = tn;
+      if (tid == 0) td[P].x = tn;
       __syncthreads();  // (3)
       // stage by tile position (piece-major) with the destination: the piece's run
       // offset + the key's place among the tile's keys of the piece
@@ -353,14 +355,15 @@ __global__ void __launch_bounds__(ScatterKeysCfg::NT, ScatterKeysCfg::MINB) k_sc
       for (int q = 0; q < R; ++q) {
         if (q * NT + tid < tn) {
           const uint32_t p = pk[q] >> 16, place = pk[q] & 0xFFFFu;
-          const uint32_t pos = tbase[p] + place;
+          const uint2 b = td[p];
+          const uint32_t pos = b.x + place;
           stage_key[pos] = x[q];
-          stage_dst[pos] = dbase[p] + place;
+          stage_dst[pos] = b.y + place;
         }
       }
       __syncthreads();  // (4)
       for (uint32_t i = tid; i < tn; i += NT) dst[stage_dst[i]] = stage_key[i];
-      for (uint32_t p = tid; p < P; p += NT) dbase[p] += tbase[p + 1] - tbase[p];
+      for (uint32_t p = tid; p < P; p += NT) td[p].y += td[p + 1].x - td[p].x;
     }
   }
 }
