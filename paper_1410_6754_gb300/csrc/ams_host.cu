@@ -504,7 +504,7 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
     ln.begin(AMS_K_BINPACK);
     AMS_TRY(ln.end(launch_binpack(la, seg_grid, s)));
     ln.begin(AMS_K_SCATTER);
-    AMS_TRY(ln.end(launch_scatter(la, p.ksize, p.pairs, /*stable=*/p.pairs, SM * (p.pairs ? 2 : 6), s)));
+    AMS_TRY(ln.end(launch_scatter(la, p.ksize, p.pairs, /*stable=*/p.pairs, SM * (p.pairs ? 2 : p.ksize == 4 ? 4 : 6), s)));
     if ((st = run_basecase(la.dst, la.vdst, lb.bc, &b.ctr[l].n_bc, 0, lp.bc_cap, false)) != AMS_OK)
       return st;
     if (la.last && (st = run_basecase(la.dst, la.vdst, b.big, &b.ctr[l].n_big, 0, p.big_cap, true)) != AMS_OK)

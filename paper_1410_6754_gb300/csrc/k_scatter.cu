@@ -204,18 +204,22 @@ __global__ void __launch_bounds__(256, 2) k_scatter(LevelArgs a) {
 // The next tile's loads and atomics need no barrier before them: the counts were
 // cleared before (3), and the stage arrays and run offsets are next written after
 // the next tile's barrier (3).
+// Shapes measured best per key width: 64-bit keys 256 threads x 12 keys, three blocks
+// per SM (80 registers, 65 KB of shared memory); 32-bit keys 512 threads x 8 keys, two
+// blocks per SM (64 registers).
+template <typename K>
 struct ScatterKeysCfg {
-  static constexpr int NT = 256;
+  static constexpr int NT = sizeof(K) == 8 ? 256 : 512;
   static constexpr int NW = NT / 32;
-  static constexpr int R = 12;  // keys per thread and tile
+  static constexpr int R = sizeof(K) == 8 ? 12 : 8;  // keys per thread and tile
   static constexpr int TILE = NT * R;
-  static constexpr int MINB = 3;  // blocks per SM (80 registers, 65 KB of shared memory)
+  static constexpr int MINB = sizeof(K) == 8 ? 3 : 2;  // blocks per SM
 };
 
 template <typename K>
 __host__ __device__ constexpr size_t scatter_keys_smem_layout(uint32_t B, size_t* off) {
   // offsets: piece_of, cnt, (tile start, run offset) pairs, unused, stage_key, stage_dst, ws
-  using C = ScatterKeysCfg;
+  using C = ScatterKeysCfg<K>;
   const uint32_t nid = 2 * B - 1;
   size_t o = 0;
   off[0] = o; o += (size_t)nid * 2;
@@ -232,8 +236,8 @@ __host__ __device__ constexpr size_t scatter_keys_smem_layout(uint32_t B, size_t
 }
 
 template <typename K>
-__global__ void __launch_bounds__(ScatterKeysCfg::NT, ScatterKeysCfg::MINB) k_scatter_keys(LevelArgs a) {
-  using Cfg = ScatterKeysCfg;
+__global__ void __launch_bounds__(ScatterKeysCfg<K>::NT, ScatterKeysCfg<K>::MINB) k_scatter_keys(LevelArgs a) {
+  using Cfg = ScatterKeysCfg<K>;
   constexpr int NT = Cfg::NT, NW = Cfg::NW, R = Cfg::R, TILE = Cfg::TILE;
   extern __shared__ __align__(16) unsigned char smem[];
   size_t off[7];
@@ -388,7 +392,7 @@ cudaError_t launch_scatter(const LevelArgs& a, int ksize, bool pairs, bool stabl
     e = cudaFuncSetAttribute(k_scatter_keys<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                              (int)sm);                                                          \
     if (e != cudaSuccess) return e;                                                             \
-    k_scatter_keys<K><<<grid, ScatterKeysCfg::NT, sm, s>>>(a);                                  \
+    k_scatter_keys<K><<<grid, ScatterKeysCfg<K>::NT, sm, s>>>(a);                               \
   } while (0)
     if (ksize == 4) AMS_LAUNCH_KEYS(uint32_t); else AMS_LAUNCH_KEYS(uint64_t);
 #undef AMS_LAUNCH_KEYS
