@@ -242,7 +242,7 @@ AMS_API ams_status ams_get_segment_tables(void* ctx, int level, uint32_t seg,
  * form: uint32_t for AMS_U32 / AMS_F32 (float keys mapped as described above) and
  * uint64_t for AMS_U64. */
 
-/* Section 6, "random sample of size abr": d_sample[j] = key[idx_j] (ordered form) for
+/* Section 6 random sample of a*b*r elements: d_sample[j] = key[idx_j] (ordered form) for
  * j < count, idx_j = floor(u_j * n / 2^64) where u_j is output j of SplitMix64 started
  * at mix(mix(seed + (level+1)*g) + (begin+1)*g), g the SplitMix64 increment. */
 AMS_API ams_status ams_step_sample(const void* d_keys, uint64_t n, ams_key_type kt, uint32_t count,
@@ -281,13 +281,21 @@ AMS_API ams_status ams_step_partition(const void* d_in, void* d_out, const uint6
                               uint64_t* d_vals_out, uint64_t n, ams_key_type kt,
                               const void* d_splitters, uint32_t nbuckets, void* stream);
 
+/* Section 6 delivery as the keys-only sorts run it: every key goes to its bucket's
+ * range of d_out (the ranges in bucket-id order, as ams_step_partition places them),
+ * in arrival order inside the range -- the paper fixes no order inside a group, and
+ * the base case orders every group.  Keys only; same arguments, errors and stream
+ * behaviour as ams_step_partition. */
+AMS_API ams_status ams_step_partition_arrival(const void* d_in, void* d_out, uint64_t n, ams_key_type kt,
+                                      const void* d_splitters, uint32_t nbuckets, void* stream);
+
 /* Section 6 base case: stable sort of n <= basecase capacity keys (and payloads) in
  * place in shared memory. */
 AMS_API ams_status ams_step_base_case(void* d_keys, uint64_t* d_vals, uint64_t n, ams_key_type kt,
                               void* stream);
 
 /* --------------------------------------------------------------- RLM-sort
- * Section 5 ("recurse last" multilevel multiway mergesort), the paper's other
+ * Section 5 (recurse-last multilevel multiway mergesort), the paper's other
  * algorithm, with perfect load balance.  Tiles of `run` consecutive positions play
  * the processing elements.  Level 0: every tile is sorted locally.  Level l (l = 1 ..
  * levels): every part of the previous level (level 0: the whole input) is split into

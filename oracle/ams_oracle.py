@@ -35,8 +35,8 @@ _MIX2 = 0x94D049BB133111EB
 
 
 # --------------------------------------------------------------------------------------
-# Counter-based generator.  READING: the paper asks for "a random sample of size abr"
-# (Section 6) without naming a generator; we draw with replacement from SplitMix64,
+# Counter-based generator.  READING: Section 6 asks for a random sample of a*b*r
+# elements without naming a generator; we draw with replacement from SplitMix64,
 # implemented here from its published definition and independently in the CUDA code.
 # --------------------------------------------------------------------------------------
 
@@ -521,7 +521,7 @@ def ams_sort(kt: int, keys: np.ndarray, pl: Plan, seed: int, vals=None, offsets=
 
 
 # --------------------------------------------------------------------------------------
-# RLM-sort (Section 5, "recurse last" multilevel multiway mergesort) and its building
+# RLM-sort (Section 5, recurse-last multilevel multiway mergesort) and its building
 # block, multisequence selection (Section 4.1).
 #
 # Sequences are sorted arrays of ordered keys (uint64); the total order among all

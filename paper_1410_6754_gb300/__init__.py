@@ -109,6 +109,7 @@ _SIGS = {
     "ams_step_classify": (_ST, [_P, _U64, _I, _P, _U32, _P, _P, _P]),
     "ams_step_bin_pack": (_ST, [_P, _U32, _U32, _P, _P, _P, _P]),
     "ams_step_partition": (_ST, [_P, _P, _P, _P, _U64, _I, _P, _U32, _P]),
+    "ams_step_partition_arrival": (_ST, [_P, _P, _U64, _I, _P, _U32, _P]),
     "ams_step_base_case": (_ST, [_P, _P, _U64, _I, _P]),
     "ams_sort_small_noalloc": (_ST, [_P, _P, _U64, _I, _P]),
     "ams_rlm_sort": (_ST, [_P, _P, _P, _P, _P, _U64, _I, _U32, _I, _PU32, _U64, _P]),
@@ -539,6 +540,16 @@ def step_partition(keys, splitters, nbuckets, vals=None, kt=None, stream=None):
                                     key_type(keys, kt), _dev(splitters), nbuckets,
                                     _stream(stream)), "ams_step_partition")
     return out if vals is None else (out, vout)
+
+
+def step_partition_arrival(keys, splitters, nbuckets, kt=None, stream=None):
+    """Keys-only delivery in arrival order inside every bucket (ams_step_partition_arrival)."""
+    torch = _torch()
+    out = torch.empty_like(keys)
+    _check(lib().ams_step_partition_arrival(_dev(keys), _dev(out), keys.numel(), key_type(keys, kt),
+                                            _dev(splitters), nbuckets, _stream(stream)),
+           "ams_step_partition_arrival")
+    return out
 
 
 def step_base_case(keys, vals=None, kt=None, stream=None):

@@ -1073,9 +1073,12 @@ static ams_status run_rlm(Context* cx, const void* kin, void* kout, const uint64
     if ((size_t)max_tiles[l] * 6 + 16 > 200u * 1024) return AMS_ERR_UNSUPPORTED;  // select windows
   // workspace: status, temporary keys (and payloads), per level part bounds, item
   // counts and items, cut table (largest level)
-  size_t cut_words = 0;
-  for (int l = 1; l <= levels; ++l)
+  size_t cut_words = 0, off_words = 0;
+  for (int l = 1; l <= levels; ++l) {
     cut_words = std::max(cut_words, (plo[l - 1].size() - 1) * (size_t)(parts[l - 1] + 1) * max_tiles[l - 1]);
+    off_words = std::max(off_words, (plo[l - 1].size() - 1) * (size_t)parts[l - 1] * max_tiles[l - 1]);
+  }
+  uint32_t* d_offs = nullptr;
   auto lay = [&](char* base, Bufs& bb, std::vector<uint32_t*>& d_plo, std::vector<uint32_t*>& d_cnt,
                  std::vector<BcItem*>& d_items, uint32_t*& d_cuts) {
     Carver c{base};
@@ -1091,6 +1094,7 @@ static ams_status run_rlm(Context* cx, const void* kin, void* kout, const uint64
       d_items[l] = c.take<BcItem>(items[l].size());
     }
     d_cuts = c.take<uint32_t>(cut_words + 1);
+    d_offs = c.take<uint32_t>(off_words + 1);
     return c.off + 256;
   };
   Bufs bb{};
@@ -1173,6 +1177,7 @@ static ams_status run_rlm(Context* cx, const void* kin, void* kout, const uint64
     ra.run = run;
     ra.max_tiles = std::max<uint32_t>(1, max_tiles[l - 1]);
     ra.cuts = d_cuts;
+    ra.offs = d_offs;
     ra.seed = seed;
     ra.level = l;
     ra.status = bb.status;
@@ -1389,9 +1394,9 @@ ams_status ams_step_bin_pack(const uint32_t* d_counts, uint32_t nbuckets, uint32
   return AMS_OK;
 }
 
-ams_status ams_step_partition(const void* d_in, void* d_out, const uint64_t* d_vals_in,
-                              uint64_t* d_vals_out, uint64_t n, ams_key_type kt,
-                              const void* d_splitters, uint32_t nbuckets, void* stream) {
+static ams_status step_partition(const void* d_in, void* d_out, const uint64_t* d_vals_in,
+                                 uint64_t* d_vals_out, uint64_t n, ams_key_type kt,
+                                 const void* d_splitters, uint32_t nbuckets, bool stable, void* stream) {
   if (!d_in || !d_out || d_in == d_out || !d_splitters || n == 0 || n >= 0xFFFFFFFFull ||
       nbuckets < 2 || nbuckets > (uint32_t)kMaxBuckets || ((d_vals_in == nullptr) != (d_vals_out == nullptr)))
     return AMS_ERR_INVALID;
@@ -1420,8 +1425,20 @@ ams_status ams_step_partition(const void* d_in, void* d_out, const uint64_t* d_v
   AMS_TRY(launch_classify(la, ks, false, cx->sm_count * 4, s));
   AMS_TRY(launch_scan(la, cx->sm_count * 8, true, s));
   AMS_TRY(launch_binpack(la, 1, s));
-  AMS_TRY(launch_scatter(la, ks, d_vals_in != nullptr, /*stable=*/true, cx->sm_count * 2, s));
+  const int grid = cx->sm_count * (stable ? 2 : ks == 4 ? 4 : 6);
+  AMS_TRY(launch_scatter(la, ks, d_vals_in != nullptr, stable, grid, s));
   return AMS_OK;
+}
+
+ams_status ams_step_partition(const void* d_in, void* d_out, const uint64_t* d_vals_in,
+                              uint64_t* d_vals_out, uint64_t n, ams_key_type kt,
+                              const void* d_splitters, uint32_t nbuckets, void* stream) {
+  return step_partition(d_in, d_out, d_vals_in, d_vals_out, n, kt, d_splitters, nbuckets, true, stream);
+}
+
+ams_status ams_step_partition_arrival(const void* d_in, void* d_out, uint64_t n, ams_key_type kt,
+                                      const void* d_splitters, uint32_t nbuckets, void* stream) {
+  return step_partition(d_in, d_out, nullptr, nullptr, n, kt, d_splitters, nbuckets, false, stream);
 }
 
 ams_status ams_step_base_case(void* d_keys, uint64_t* d_vals, uint64_t n, ams_key_type kt, void* stream) {

@@ -1,4 +1,4 @@
-// RLM-sort (Section 5, "recurse last" multilevel multiway mergesort) on one GPU: the
+// RLM-sort (Section 5, recurse-last multilevel multiway mergesort) on one GPU: the
 // two kernels of a level besides the tile sorts (which are the base-case kernel).
 //
 // A processing element's data is a tile of `run` consecutive positions of a part.
@@ -7,8 +7,8 @@
 //       the cuts, in the order (key, tile, position) -- which is (key, original index)
 //       because tiles hold consecutive ranges and every tile is sorted stably.
 //       Quickselect on sorted sequences: every tile keeps a window [lo, hi) that holds
-//       its cut; each round draws a pivot uniformly from the windows' elements
-//       (SplitMix64 stream of the (level, part, rank)), finds by binary search in every
+//       its cut; each round picks a pivot from the windows' elements (SplitMix64 stream
+//       of the (level, part, rank); see pivot_pos), finds by binary search in every
 //       window how many elements precede the pivot, and either takes the pivot and
 //       everything before it (fewer than k precede it) or ends the windows at it.
 //   deliver (Section 5 data delivery)  one block per (part, new part j): the piece of
@@ -27,6 +27,19 @@ __device__ __forceinline__ uint64_t rlm_mix(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
+}
+
+// Offset of the pivot inside the chosen tile's window of `len` elements.  Odd rounds:
+// the drawn element (offset `rem`, a uniformly random element of all windows -- the
+// paper's quickselect).  Even rounds: the element at the target's fraction of the
+// window, `need` of the `total` window elements being wanted -- close to the target
+// when the tile's values are spread like the part's, and no worse than a random pick
+// otherwise (the tile is still drawn with probability proportional to its window).
+// Any pivot gives the same cuts; this one needs fewer rounds.
+__device__ __forceinline__ uint32_t pivot_pos(uint32_t round, uint32_t rem, uint32_t len, uint32_t need,
+                                              uint32_t total) {
+  if (round & 1) return rem;
+  return min(len - 1, (uint32_t)(((uint64_t)need * len) / total));
 }
 
 template <typename K>
@@ -71,7 +84,9 @@ __global__ void __launch_bounds__(kSelThreads) k_multiselect(RlmArgs a) {
         if (tid == 0) atomicOr(a.status, ST_OVERFLOW);
         break;
       }
-      // pivot: element number u of the windows, in (thread, tile) order
+      // pivot: element number u of the windows, in (thread, tile) order; on even
+      // rounds, in the tile that holds element u, the element at the target's fraction
+      // (k - taken) / total of that tile's window instead (pivot_pos)
       state += 0x9E3779B97F4A7C15ull;
       const uint32_t u = (uint32_t)__umul64hi(rlm_mix(state), (uint64_t)total);
       if (u >= wpre && u < wpre + wsum) {
@@ -79,7 +94,7 @@ __global__ void __launch_bounds__(kSelThreads) k_multiselect(RlmArgs a) {
         for (uint32_t t = tid; t < T; t += NT) {
           const uint32_t len = whi[t] - wlo[t];
           if (rem < len) {
-            const uint32_t pos = wlo[t] + rem;
+            const uint32_t pos = wlo[t] + pivot_pos(round, rem, len, k - taken_all, total);
             piv_key = (unsigned long long)keys[plo + t * a.run + pos];
             piv_tile = t;
             piv_pos = pos;
@@ -145,6 +160,125 @@ __global__ void __launch_bounds__(kSelThreads) k_multiselect(RlmArgs a) {
   }
 }
 
+// The same selection by one warp, for parts of at most kWarpTiles tiles (the deeper
+// levels: a part of m keys has about m / run tiles, so many small selections).  Lane l
+// keeps the windows of tiles l, l + 32, ... in registers; sums and counts are warp
+// reductions, so there is no block barrier and a block runs kSelThreads / 32
+// selections side by side.  The pivot stream and the take / shrink rule are those of
+// the block version (the elements are numbered in (lane, tile) order); the cuts do
+// not depend on the pivots.
+constexpr uint32_t kWarpTilesPerLane = 8;
+constexpr uint32_t kWarpTiles = 32 * kWarpTilesPerLane;
+
+template <typename K>
+__global__ void __launch_bounds__(kSelThreads) k_multiselect_warp(RlmArgs a) {
+  constexpr uint32_t PT = kWarpTilesPerLane;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t per_part = a.r - 1;
+  const uint32_t wpb = blockDim.x / 32;
+  const K* keys = (const K*)a.src;
+  for (uint32_t job = blockIdx.x * wpb + (threadIdx.x >> 5); job < a.nparts * per_part; job += gridDim.x * wpb) {
+    const uint32_t part = job / per_part, j = job % per_part + 1;
+    const uint32_t plo = a.part_lo[part], m = a.part_lo[part + 1] - plo;
+    const uint32_t T = (m + a.run - 1) / a.run;  // <= kWarpTiles (checked by the launcher)
+    const uint32_t k = (uint32_t)(((uint64_t)j * m) / a.r);
+    uint32_t wlo[PT], whi[PT];
+#pragma unroll
+    for (uint32_t i = 0; i < PT; ++i) {
+      const uint32_t t = lane + 32 * i;
+      wlo[i] = 0;
+      whi[i] = t < T ? min(a.run, m - t * a.run) : 0u;
+    }
+    uint64_t state = rlm_mix(a.seed + (uint64_t)(a.level + 1) * 0x9E3779B97F4A7C15ull);
+    state = rlm_mix(state + (((uint64_t)part << 32) | j));
+    for (uint32_t round = 0;; ++round) {
+      uint32_t wsum = 0, taken = 0;
+#pragma unroll
+      for (uint32_t i = 0; i < PT; ++i) {
+        wsum += whi[i] - wlo[i];
+        taken += wlo[i];
+      }
+      uint32_t incl = wsum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+      }
+      const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+      const uint32_t taken_all = __reduce_add_sync(0xFFFFFFFFu, taken);
+      if (taken_all == k) break;  // (warp-uniform)
+      if (total == 0 || round == kSelMaxRounds) {  // cannot happen on consistent input
+        if (lane == 0) atomicOr(a.status, ST_OVERFLOW);
+        break;
+      }
+      state += 0x9E3779B97F4A7C15ull;
+      const uint32_t u = (uint32_t)__umul64hi(rlm_mix(state), (uint64_t)total);
+      // the lane whose elements hold number u names the pivot
+      const uint32_t wpre = incl - wsum;
+      uint32_t pt = 0xFFFFFFFFu, pp = 0;
+      if (u >= wpre && u < incl) {
+        uint32_t rem = u - wpre;
+#pragma unroll
+        for (uint32_t i = 0; i < PT; ++i) {
+          const uint32_t len = whi[i] - wlo[i];
+          if (pt == 0xFFFFFFFFu) {
+            if (rem < len) {
+              pt = lane + 32 * i;
+              pp = wlo[i] + pivot_pos(round, rem, len, k - taken_all, total);
+            } else {
+              rem -= len;
+            }
+          }
+        }
+      }
+      const uint32_t owner = __ffs(__ballot_sync(0xFFFFFFFFu, pt != 0xFFFFFFFFu)) - 1;
+      pt = __shfl_sync(0xFFFFFFFFu, pt, owner);
+      pp = __shfl_sync(0xFFFFFFFFu, pp, owner);
+      const K pk = keys[plo + pt * a.run + pp];  // (every lane loads the same word)
+      // elements of each window before the pivot in (key, tile, position) order
+      uint32_t lo[PT], hi[PT];
+#pragma unroll
+      for (uint32_t i = 0; i < PT; ++i) {
+        const uint32_t t = lane + 32 * i;
+        lo[i] = wlo[i];
+        hi[i] = whi[i];
+        if (t == pt) lo[i] = hi[i] = min(max(pp, lo[i]), hi[i]);
+      }
+      for (;;) {
+        bool active = false;
+#pragma unroll
+        for (uint32_t i = 0; i < PT; ++i) {
+          if (lo[i] < hi[i]) {
+            const uint32_t t = lane + 32 * i;
+            const uint32_t mid = (lo[i] + hi[i]) >> 1;
+            const K v = keys[plo + t * a.run + mid];
+            if (t < pt ? v <= pk : v < pk) lo[i] = mid + 1; else hi[i] = mid;
+            active = true;
+          }
+        }
+        if (!active) break;
+      }
+      uint32_t cnt = 0;
+#pragma unroll
+      for (uint32_t i = 0; i < PT; ++i) cnt += lo[i];
+      const uint32_t before_all = __reduce_add_sync(0xFFFFFFFFu, cnt);
+      const bool take = before_all < k;  // the pivot and all before it are among the first k
+#pragma unroll
+      for (uint32_t i = 0; i < PT; ++i) {
+        const uint32_t t = lane + 32 * i;
+        if (take) wlo[i] = t == pt ? pp + 1 : lo[i];
+        else whi[i] = lo[i];
+      }
+    }
+    uint32_t* row = a.cuts + ((size_t)part * (a.r + 1) + j) * a.max_tiles;
+#pragma unroll
+    for (uint32_t i = 0; i < PT; ++i) {
+      const uint32_t t = lane + 32 * i;
+      if (t < T) row[t] = wlo[i];
+    }
+  }
+}
+
 // Cut rows 0 and r of every part: the tile starts and ends.
 __global__ void k_rlm_cut_ends(RlmArgs a) {
   for (uint32_t part = blockIdx.x; part < a.nparts; part += gridDim.x) {
@@ -159,38 +293,96 @@ __global__ void k_rlm_cut_ends(RlmArgs a) {
   }
 }
 
-// New part j of `part`: its pieces, one per tile in tile order, go to
-// [part_lo + floor(j m / r), ...); warp w copies the pieces of tiles w, w + NW, ...
-template <typename K, bool PAIRS>
-__global__ void __launch_bounds__(512) k_deliver(RlmArgs a) {
-  constexpr int NT = 512, NW = NT / 32;
+// Where each piece of new part j of `part` starts inside the new part: the exclusive
+// prefix of the piece sizes in tile order (one block per (part, j)); the pieces then
+// fill [floor(j m / r), floor((j + 1) m / r)) of the part exactly.
+__global__ void __launch_bounds__(512) k_rlm_offsets(RlmArgs a) {
+  constexpr int NT = 512;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* off = (uint32_t*)smem;  // max_tiles + 1 piece offsets
   __shared__ uint32_t ws[NT / 32 + 1];
-  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const K* src = (const K*)a.src;
-  K* dst = (K*)a.dst;
   for (uint32_t job = blockIdx.x; job < a.nparts * a.r; job += gridDim.x) {
     const uint32_t part = job / a.r, j = job % a.r;
-    const uint32_t plo = a.part_lo[part], m = a.part_lo[part + 1] - plo;
+    const uint32_t m = a.part_lo[part + 1] - a.part_lo[part];
     const uint32_t T = (m + a.run - 1) / a.run;
     const uint32_t* c0 = a.cuts + ((size_t)part * (a.r + 1) + j) * a.max_tiles;
     const uint32_t* c1 = c0 + a.max_tiles;
     for (uint32_t t = threadIdx.x; t < T; t += NT) off[t] = c1[t] - c0[t];
     __syncthreads();
     const uint32_t total = block_scan_array<NT, uint32_t>(off, T, ws);  // (ends with a barrier)
-    const uint32_t out0 = plo + (uint32_t)(((uint64_t)j * m) / a.r);
-    if (threadIdx.x == 0 && out0 + total != plo + (uint32_t)(((uint64_t)(j + 1) * m) / a.r))
+    if (threadIdx.x == 0 &&
+        total != (uint32_t)(((uint64_t)(j + 1) * m) / a.r) - (uint32_t)(((uint64_t)j * m) / a.r))
       atomicOr(a.status, ST_OVERFLOW);  // cuts inconsistent with the ranks (never expected)
-    for (uint32_t t = w; t < T; t += NW) {
-      const uint32_t b = plo + t * a.run + c0[t], len = c1[t] - c0[t];
-      const uint32_t o = out0 + off[t];
-      for (uint32_t i = lane; i < len; i += 32) {
-        dst[o + i] = src[b + i];
-        if constexpr (PAIRS) a.vdst[o + i] = a.vsrc[b + i];
+    uint32_t* row = a.offs + ((size_t)part * a.r + j) * a.max_tiles;
+    for (uint32_t t = threadIdx.x; t < T; t += NT) row[t] = off[t];
+    __syncthreads();
+  }
+}
+
+// Delivery: one warp per 32 consecutive tiles of one (part, new part j).  Their pieces
+// are consecutive in the new part, so the warp copies one contiguous output range:
+// output element o belongs to the last of the 32 pieces whose offset is <= o (a
+// five-step search over the offsets held by the lanes), four elements per lane in
+// flight.
+template <typename K, bool PAIRS>
+__global__ void __launch_bounds__(256) k_deliver(RlmArgs a) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t tb_per = (a.max_tiles + 31) / 32;
+  const uint64_t tasks = (uint64_t)a.nparts * a.r * tb_per;
+  const K* src = (const K*)a.src;
+  K* dst = (K*)a.dst;
+  for (uint64_t task = (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); task < tasks;
+       task += (uint64_t)gridDim.x * (blockDim.x / 32)) {
+    const uint32_t tb = (uint32_t)(task % tb_per);
+    const uint32_t pj = (uint32_t)(task / tb_per);
+    const uint32_t part = pj / a.r, j = pj % a.r;
+    const uint32_t plo = a.part_lo[part], m = a.part_lo[part + 1] - plo;
+    const uint32_t T = (m + a.run - 1) / a.run;
+    if (tb * 32 >= T) continue;  // (warp-uniform)
+    const uint32_t t = tb * 32 + lane;
+    const bool has = t < T;
+    const uint32_t* c0 = a.cuts + ((size_t)part * (a.r + 1) + j) * a.max_tiles;
+    const uint32_t cut0 = has ? c0[t] : 0u, cut1 = has ? c0[a.max_tiles + t] : 0u;
+    const uint32_t poff = has ? a.offs[((size_t)part * a.r + j) * a.max_tiles + t] : 0u;
+    const uint32_t len = cut1 - cut0;
+    const uint32_t sbeg = plo + t * a.run + cut0;  // (unused when !has)
+    // the warp's output range, relative to its first piece
+    const uint32_t base = __shfl_sync(0xFFFFFFFFu, poff, 0);
+    const uint32_t rel = has ? poff - base : 0xFFFFFFFFu;  // pieces past T never match
+    const uint32_t last = min(T - tb * 32, 32u) - 1;
+    const uint32_t L = __shfl_sync(0xFFFFFFFFu, rel + len, last);
+    const uint32_t out0 = plo + (uint32_t)(((uint64_t)j * m) / a.r) + base;
+    for (uint32_t o0 = 0; o0 < L; o0 += 128) {
+      K v[4];
+      uint64_t pv[PAIRS ? 4 : 1];
+      uint32_t oo[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t o = o0 + u * 32 + lane;
+        oo[u] = o;
+        // piece p holding o: the largest p with rel[p] <= o (rel[0] = 0)
+        uint32_t p = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const uint32_t q = p + step;
+          const uint32_t rq = __shfl_sync(0xFFFFFFFFu, rel, q & 31);
+          if (q <= last && rq <= o) p = q;
+        }
+        const uint32_t sb = __shfl_sync(0xFFFFFFFFu, sbeg, p);
+        const uint32_t rp = __shfl_sync(0xFFFFFFFFu, rel, p);
+        if (o < L) {
+          v[u] = src[sb + (o - rp)];
+          if constexpr (PAIRS) pv[u] = a.vsrc[sb + (o - rp)];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (oo[u] < L) {
+          dst[out0 + oo[u]] = v[u];
+          if constexpr (PAIRS) a.vdst[out0 + oo[u]] = pv[u];
+        }
       }
     }
-    __syncthreads();
   }
 }
 
@@ -204,19 +396,28 @@ cudaError_t launch_rlm_level(const RlmArgs& a, int ksize, bool pairs, int sm_cou
   const size_t ssel = rlm_select_smem(a.max_tiles), sdel = rlm_deliver_smem(a.max_tiles);
   const int gsel = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)a.nparts * (a.r - 1), (uint64_t)sm_count * 8));
   const int gdel = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)a.nparts * a.r, (uint64_t)sm_count * 8));
+  const uint64_t copy_tasks = (uint64_t)a.nparts * a.r * ((a.max_tiles + 31) / 32);
+  const int gcopy = (int)std::max<uint64_t>(1, std::min<uint64_t>((copy_tasks + 7) / 8, (uint64_t)sm_count * 8));
+  if ((e = cudaFuncSetAttribute(k_rlm_offsets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sdel)) !=
+      cudaSuccess)
+    return e;
+  const uint64_t wjobs = ((uint64_t)a.nparts * (a.r - 1) + kSelThreads / 32 - 1) / (kSelThreads / 32);
+  const int gselw = (int)std::max<uint64_t>(1, std::min<uint64_t>(wjobs, (uint64_t)sm_count * 4));
 #define AMS_RLM_LAUNCH(K, P)                                                                      \
   do {                                                                                            \
-    if (a.r > 1) {                                                                                \
+    if (a.r > 1 && a.max_tiles <= kWarpTiles) {                                                   \
+      k_multiselect_warp<K><<<gselw, kSelThreads, 0, s>>>(a);                                     \
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;                                      \
+    } else if (a.r > 1) {                                                                         \
       if ((e = cudaFuncSetAttribute(k_multiselect<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                     (int)ssel)) != cudaSuccess)                                   \
         return e;                                                                                 \
       k_multiselect<K><<<gsel, kSelThreads, ssel, s>>>(a);                                        \
       if ((e = cudaGetLastError()) != cudaSuccess) return e;                                      \
     }                                                                                             \
-    if ((e = cudaFuncSetAttribute(k_deliver<K, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                  (int)sdel)) != cudaSuccess)                                     \
-      return e;                                                                                   \
-    k_deliver<K, P><<<gdel, 512, sdel, s>>>(a);                                                   \
+    k_rlm_offsets<<<gdel, 512, sdel, s>>>(a);                                                     \
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;                                        \
+    k_deliver<K, P><<<gcopy, 256, 0, s>>>(a);                                                     \
   } while (0)
   if (ksize == 4) {
     if (pairs) AMS_RLM_LAUNCH(uint32_t, true); else AMS_RLM_LAUNCH(uint32_t, false);

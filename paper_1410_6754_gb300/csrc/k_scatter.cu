@@ -1,4 +1,4 @@
-// Delivery of one distribution level (Section 6 "data delivery" of the bucket groups;
+// Delivery of one distribution level (Section 6 data delivery of the bucket groups;
 // prefix-sum delivery of Section 4.3).  Every key goes to its *piece* (a run of
 // buckets of one group, or a final equality bucket -- made by the bin-packing
 // kernel) at: piece start + the keys of that piece in earlier chunks (from the

@@ -17,6 +17,7 @@ struct RlmArgs {
   uint32_t run;             // tile size
   uint32_t max_tiles;       // largest tile count of a part (cut-table row stride)
   uint32_t* cuts;           // [nparts][r + 1][max_tiles] cut positions inside the tiles
+  uint32_t* offs;           // [nparts][r][max_tiles] where each piece starts in its new part
   uint64_t seed;
   int level;
   uint32_t* status;

@@ -21,7 +21,7 @@ def test_header_declares_the_boundary():
                  "ams_sort_pairs_into", "ams_sort_host", "ams_context_create",
                  "ams_context_destroy", "ams_sort_request", "ams_context_sync", "ams_get_stats",
                  "ams_step_sample", "ams_step_rank_sort", "ams_step_splitters",
-                 "ams_step_classify", "ams_step_bin_pack", "ams_step_partition",
+                 "ams_step_classify", "ams_step_bin_pack", "ams_step_partition", "ams_step_partition_arrival",
                  "ams_step_base_case", "ams_status_string", "ams_version"]:
         assert name in syms
 

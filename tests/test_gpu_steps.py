@@ -184,6 +184,28 @@ def test_partition(kt, bits, pairs, n, B):
 
 
 @pytest.mark.parametrize("kt,bits", KTS)
+@pytest.mark.parametrize("dist", ["uniform", "zipf", "sorted"])
+@pytest.mark.parametrize("n,B", [(5000, 2), (100003, 256), (1 << 20, 1024), (262147, 2048)])
+def test_partition_arrival(kt, bits, dist, n, B):
+    """The keys-only delivery the sorts use: every bucket's range holds exactly the
+    bucket's keys (the oracle's stable partition, compared as a multiset per bucket,
+    since the order inside a bucket is arrival order)."""
+    dt = ordered_dtype(kt)
+    keys = _keys(kt, bits, dist, n, n + 7)
+    t = O.ordered_keys(kt, keys)
+    rng = np.random.default_rng(n + B)
+    spl = np.sort(t[rng.integers(0, n, size=B - 1)])
+    out = to_np(ams.step_partition_arrival(to_dev(keys), to_dev(spl.astype(dt)), B, kt=kt), dt)
+    torch.cuda.synchronize()
+    ids = O.classify(spl, B, t)
+    expect = t[O.stable_partition(ids)].astype(dt)
+    bucket_of_pos = np.repeat(np.arange(2 * B - 1), O.bucket_counts(ids, B))
+    o1 = np.lexsort((out, bucket_of_pos))
+    o2 = np.lexsort((expect, bucket_of_pos))
+    assert same_bits(out[o1], expect[o2])
+
+
+@pytest.mark.parametrize("kt,bits", KTS)
 @pytest.mark.parametrize("pairs", [False, True])
 def test_base_case(kt, bits, pairs):
     cap = ams.default_basecase_cap(kt, pairs)
