@@ -524,8 +524,10 @@ __global__ void __launch_bounds__(512, BaseCfg<K, PAIRS>::MINB) k_basecase(BaseA
   if (sortable(item)) load_item<K, PAIRS>(src, item.begin, item.end - item.begin, a.tf_load, x);
   for (uint32_t it = blockIdx.x; it < nitems; it += gridDim.x) {
     const BcItem nxt = it + gridDim.x < nitems ? a.items[it + gridDim.x] : none;
-    if (threadIdx.x == 0 && sortable(nxt))  // the next item's keys into L2 now
+    if (threadIdx.x == 0 && sortable(nxt)) {  // the next item's keys (and payloads) into L2 now
       prefetch_l2(src + nxt.begin, (size_t)(nxt.end - nxt.begin) * sizeof(K));
+      if constexpr (PAIRS) prefetch_l2(a.vsrc + nxt.begin, (size_t)(nxt.end - nxt.begin) * 8);
+    }
     auto prefetch = [&] {
       if (sortable(nxt)) load_item<K, PAIRS>(src, nxt.begin, nxt.end - nxt.begin, a.tf_load, x);
     };

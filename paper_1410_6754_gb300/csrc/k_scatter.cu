@@ -106,6 +106,12 @@ __global__ void __launch_bounds__(256, 2) k_scatter(LevelArgs a) {
 
     for (uint32_t t0 = lo; t0 < hi; t0 += TILE) {
       const uint32_t tn = min((uint32_t)TILE, hi - t0);
+      if (tid == 0 && t0 + TILE < hi) {  // the next tile's keys, ids and payloads into L2
+        const uint32_t nn = min((uint32_t)TILE, hi - (t0 + TILE));
+        prefetch_l2(src + t0 + TILE, (size_t)nn * sizeof(K));
+        prefetch_l2(ids + t0 + TILE, (size_t)nn * 2);
+        if constexpr (PAIRS) prefetch_l2(a.vsrc + t0 + TILE, (size_t)nn * 8);
+      }
       // counters of pieces 0..P (P = the dummy piece of the tile's empty slots)
       {
         const uint32_t hw = (P + 2) / 2;  // 32-bit words per warp row
