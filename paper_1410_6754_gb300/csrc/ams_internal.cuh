@@ -24,6 +24,7 @@ namespace ams {
 
 constexpr int kMaxLevels = 8;
 constexpr int kSampleTile = 2048;       // keys per locally sorted sample tile
+constexpr uint32_t kRankCols = 4;       // column tiles one cross-rank unit ranks a row tile against
 constexpr uint32_t kCopyChunk = 65536;  // elements per copy work item
 constexpr int kMaxBuckets = 2048;       // largest b*r per level
 constexpr uint32_t kCellTable = 16384;  // cells of the table classifier
@@ -49,7 +50,7 @@ struct SegInfo {
   uint32_t a, S, T;   // oversampling factor, sample size a*B, sample tiles
   uint32_t samp_off;  // first sample of the segment
   uint32_t tile_off;  // first sample tile
-  uint32_t pair_off;  // first (row tile, column tile) pair, T*(T-1) pairs
+  uint32_t pair_off;  // first cross-rank unit: T row tiles x ceil((T-1)/kRankCols) column groups
   uint32_t item_off;  // first classify/scatter chunk
   uint32_t nitems;
 };

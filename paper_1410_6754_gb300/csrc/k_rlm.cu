@@ -29,18 +29,38 @@ __device__ __forceinline__ uint64_t rlm_mix(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-// Offset of the pivot inside the chosen tile's window of `len` elements.  Odd rounds:
-// the drawn element (offset `rem`, a uniformly random element of all windows -- the
-// paper's quickselect).  Even rounds: the element at the target's fraction of the
-// window, `need` of the `total` window elements being wanted -- close to the target
-// when the tile's values are spread like the part's, and no worse than a random pick
-// otherwise (the tile is still drawn with probability proportional to its window).
-// Any pivot gives the same cuts; this one needs fewer rounds.
-__device__ __forceinline__ uint32_t pivot_pos(uint32_t round, uint32_t rem, uint32_t len, uint32_t need,
+// Offset of the pivot inside the chosen tile's window of `len` elements.  Otherwise
+// than the paper's random pivot (the drawn element itself, offset `rem`: a uniformly
+// random element of all windows), a targeted round aims just past the target: the
+// target is element `need` of the `total` window elements, its fraction f = need /
+// total; the tile's element at fraction f estimates it with a standard deviation of
+// about sqrt(f (1 - f) / len), so the pivot is taken three of those (plus one element)
+// beyond f, on the side of the larger part -- which the round then cuts away, so two
+// rounds bracket the target from both sides (the idea of Floyd and Rivest's
+// selection).  The tile is drawn with probability proportional to its window either
+// way.  Any pivot gives the same cuts; targeted pivots need far fewer rounds on evenly
+// spread keys.
+__device__ __forceinline__ uint32_t pivot_pos(bool targeted, uint32_t rem, uint32_t len, uint32_t need,
                                               uint32_t total) {
-  if (round & 1) return rem;
-  return min(len - 1, (uint32_t)(((uint64_t)need * len) / total));
+  if (!targeted) return rem;
+  const float f = (float)need / (float)total;
+  const float d = 3.0f * sqrtf(f * (1.0f - f) / (float)len) + 1.0f / (float)len;
+  const float g = fminf(1.0f, fmaxf(0.0f, f < 0.5f ? f + d : f - d));
+  return min(len - 1, (uint32_t)(g * (float)len));
 }
+
+// Pivot rule of the next round: targeted, unless the last round was targeted and
+// did not halve the windows (then one random round, as in the paper).
+struct PivotRule {
+  bool targeted = true;
+  uint32_t before = 0xFFFFFFFFu;  // window total when the last round started
+  __device__ __forceinline__ bool next(uint32_t total) {
+    const bool t = !(targeted && before != 0xFFFFFFFFu && (uint64_t)total * 2 > before);
+    targeted = t;
+    before = total;
+    return t;
+  }
+};
 
 template <typename K>
 __global__ void __launch_bounds__(kSelThreads) k_multiselect(RlmArgs a) {
@@ -68,6 +88,7 @@ __global__ void __launch_bounds__(kSelThreads) k_multiselect(RlmArgs a) {
     uint64_t state = rlm_mix(a.seed + (uint64_t)(a.level + 1) * 0x9E3779B97F4A7C15ull);
     state = rlm_mix(state + (((uint64_t)part << 32) | j));
     __syncthreads();
+    PivotRule rule;
     for (uint32_t round = 0;; ++round) {
       // window sizes and the elements already taken, over this thread's tiles
       // t = tid, tid + NT, ...
@@ -84,9 +105,10 @@ __global__ void __launch_bounds__(kSelThreads) k_multiselect(RlmArgs a) {
         if (tid == 0) atomicOr(a.status, ST_OVERFLOW);
         break;
       }
-      // pivot: element number u of the windows, in (thread, tile) order; on even
-      // rounds, in the tile that holds element u, the element at the target's fraction
-      // (k - taken) / total of that tile's window instead (pivot_pos)
+      // pivot: element number u of the windows, in (thread, tile) order, or, in a
+      // targeted round, in the tile that holds element u, the element at the target's
+      // fraction (k - taken) / total of that tile's window (pivot_pos)
+      const bool targeted = rule.next(total);
       state += 0x9E3779B97F4A7C15ull;
       const uint32_t u = (uint32_t)__umul64hi(rlm_mix(state), (uint64_t)total);
       if (u >= wpre && u < wpre + wsum) {
@@ -94,7 +116,7 @@ __global__ void __launch_bounds__(kSelThreads) k_multiselect(RlmArgs a) {
         for (uint32_t t = tid; t < T; t += NT) {
           const uint32_t len = whi[t] - wlo[t];
           if (rem < len) {
-            const uint32_t pos = wlo[t] + pivot_pos(round, rem, len, k - taken_all, total);
+            const uint32_t pos = wlo[t] + pivot_pos(targeted, rem, len, k - taken_all, total);
             piv_key = (unsigned long long)keys[plo + t * a.run + pos];
             piv_tile = t;
             piv_pos = pos;
@@ -191,6 +213,7 @@ __global__ void __launch_bounds__(kSelThreads) k_multiselect_warp(RlmArgs a) {
     }
     uint64_t state = rlm_mix(a.seed + (uint64_t)(a.level + 1) * 0x9E3779B97F4A7C15ull);
     state = rlm_mix(state + (((uint64_t)part << 32) | j));
+    PivotRule rule;
     for (uint32_t round = 0;; ++round) {
       uint32_t wsum = 0, taken = 0;
 #pragma unroll
@@ -211,6 +234,7 @@ __global__ void __launch_bounds__(kSelThreads) k_multiselect_warp(RlmArgs a) {
         if (lane == 0) atomicOr(a.status, ST_OVERFLOW);
         break;
       }
+      const bool targeted = rule.next(total);
       state += 0x9E3779B97F4A7C15ull;
       const uint32_t u = (uint32_t)__umul64hi(rlm_mix(state), (uint64_t)total);
       // the lane whose elements hold number u names the pivot
@@ -224,7 +248,7 @@ __global__ void __launch_bounds__(kSelThreads) k_multiselect_warp(RlmArgs a) {
           if (pt == 0xFFFFFFFFu) {
             if (rem < len) {
               pt = lane + 32 * i;
-              pp = wlo[i] + pivot_pos(round, rem, len, k - taken_all, total);
+              pp = wlo[i] + pivot_pos(targeted, rem, len, k - taken_all, total);
             } else {
               rem -= len;
             }

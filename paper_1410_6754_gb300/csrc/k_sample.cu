@@ -13,8 +13,8 @@ namespace ams {
 // ----------------------------------------------------------------------------- setup
 // One block of 1024 threads.  Reads the segment count of the level, computes for
 // every segment a = min(a_rule(n_g), max(1, n_g / (16 B))), S = a B, the number of
-// sample tiles T = ceil(S / 2048), T (T-1) tile pairs and ceil(n_g / CH) chunks,
-// and exclusive prefixes of all four.  On a capacity overflow the level is emptied
+// sample tiles T = ceil(S / 2048), T ceil((T-1) / kRankCols) cross-rank units and
+// ceil(n_g / CH) chunks, and exclusive prefixes of all four.  On a capacity overflow the level is emptied
 // and the status word flagged, so that no later kernel writes out of bounds.
 __global__ void __launch_bounds__(1024) k_setup(LevelArgs a) {
   __shared__ uint32_t ws[4][33];
@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(1024) k_setup(LevelArgs a) {
       const uint32_t T = (S + kSampleTile - 1) / kSampleTile;
       v[0] = S;
       v[1] = T;
-      v[2] = T * (T - 1);
+      v[2] = T * ((T - 1 + kRankCols - 1) / kRankCols);  // (row tile, column group) units
       v[3] = (ng + a.CH - 1) / a.CH;
     }
     uint32_t off[4], tot[4];
@@ -148,40 +148,62 @@ __global__ void __launch_bounds__(512) k_sample_sort(LevelArgs a, K* raw_out, co
 }
 
 // ------------------------------------------------------------------------ cross rank
-// Pair (i, j), i != j, of tiles of one segment: every element v of sorted tile i gets
+// Unit (i, c) of one segment: row tile i against the column tiles j != i of group c
+// (kRankCols of them).  Every element v of sorted tile i gets, summed over those j,
 // the number of elements of tile j that precede it in the (key, slot) order, i.e.
-// #{y < v} if j > i (later slots) and #{y <= v} if j < i (earlier slots).
+// #{y < v} if j > i (later slots) and #{y <= v} if j < i (earlier slots); the row's
+// elements stay in registers across the group's columns and are added to their rank
+// with one atomic each.
 template <typename K>
 __global__ void __launch_bounds__(512) k_cross_rank(LevelArgs a) {
-  constexpr int NT = 512;
+  constexpr int NT = 512, EPT = kSampleTile / NT;
   __shared__ K tile_s[kSampleTile];
   const uint32_t nseg = a.ctr->nseg;
-  const uint32_t pairs = a.ctr->pairs;
+  const uint32_t units = a.ctr->pairs;
   const K* samp = (const K*)a.sample;
-  for (uint32_t p = blockIdx.x; p < pairs; p += gridDim.x) {
+  for (uint32_t p = blockIdx.x; p < units; p += gridDim.x) {
     const uint32_t g = find_seg<&SegInfo::pair_off>(a.sinfo, nseg, p);
     const SegInfo si = a.sinfo[g];
+    const uint32_t ngroups = (si.T - 1 + kRankCols - 1) / kRankCols;
     const uint32_t q = p - si.pair_off;
-    const uint32_t i = q / (si.T - 1);
-    const uint32_t jj = q % (si.T - 1);
-    const uint32_t j = jj < i ? jj : jj + 1;
+    const uint32_t i = q / ngroups, c = q % ngroups;
     const uint32_t ci = min((uint32_t)kSampleTile, si.S - i * kSampleTile);
-    const uint32_t cj = min((uint32_t)kSampleTile, si.S - j * kSampleTile);
     const K* ti = samp + si.samp_off + i * kSampleTile;
-    const K* tj = samp + si.samp_off + j * kSampleTile;
-    for (uint32_t e = threadIdx.x; e < cj; e += NT) tile_s[e] = tj[e];
-    __syncthreads();
-    const bool inclusive = j < i;
-    for (uint32_t e = threadIdx.x; e < ci; e += NT) {
-      const K v = ti[e];
-      uint32_t lo = 0, hi = cj;  // first position whose key is > v (inclusive) / >= v
-      while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        const K y = tile_s[mid];
-        const bool before = inclusive ? (y <= v) : (y < v);
-        if (before) lo = mid + 1; else hi = mid;
+    K v[EPT];
+    uint32_t acc[EPT];
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const uint32_t e = threadIdx.x + u * NT;
+      v[u] = e < ci ? ti[e] : K(0);
+      acc[u] = 0;
+    }
+    const uint32_t jj_end = min((c + 1) * kRankCols, si.T - 1);
+    for (uint32_t jj = c * kRankCols; jj < jj_end; ++jj) {
+      const uint32_t j = jj < i ? jj : jj + 1;
+      const uint32_t cj = min((uint32_t)kSampleTile, si.S - j * kSampleTile);
+      const K* tj = samp + si.samp_off + j * kSampleTile;
+      __syncthreads();  // (the previous column's searches are done)
+      for (uint32_t e = threadIdx.x; e < cj; e += NT) tile_s[e] = tj[e];
+      __syncthreads();
+      const bool inclusive = j < i;
+#pragma unroll
+      for (int u = 0; u < EPT; ++u) {
+        if (threadIdx.x + u * NT < ci) {
+          uint32_t lo = 0, hi = cj;  // first position whose key is > v (inclusive) / >= v
+          while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            const K y = tile_s[mid];
+            const bool before = inclusive ? (y <= v[u]) : (y < v[u]);
+            if (before) lo = mid + 1; else hi = mid;
+          }
+          acc[u] += lo;
+        }
       }
-      atomicAdd(&a.srank[si.samp_off + i * kSampleTile + e], lo);
+    }
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const uint32_t e = threadIdx.x + u * NT;
+      if (e < ci && acc[u]) atomicAdd(&a.srank[si.samp_off + i * kSampleTile + e], acc[u]);
     }
     __syncthreads();
   }
