@@ -20,7 +20,8 @@
 
 namespace ams {
 
-constexpr int kSelThreads = 512;
+constexpr int kSelThreads = 512;        // warp selections: 16 per block
+constexpr int kSelBlockThreads = 1024;  // one selection per block: more binary searches in flight
 constexpr uint32_t kSelMaxRounds = 4096;  // guard: quickselect ends in O(log n) rounds
 
 __device__ __forceinline__ uint64_t rlm_mix(uint64_t z) {
@@ -63,8 +64,8 @@ struct PivotRule {
 };
 
 template <typename K>
-__global__ void __launch_bounds__(kSelThreads) k_multiselect(RlmArgs a) {
-  constexpr int NT = kSelThreads;
+__global__ void __launch_bounds__(kSelBlockThreads) k_multiselect(RlmArgs a) {
+  constexpr int NT = kSelBlockThreads;
   constexpr int G = 8;  // binary searches of one thread interleaved (independent loads)
   extern __shared__ __align__(16) unsigned char smem[];
   uint16_t* wlo = (uint16_t*)smem;  // window of every tile (positions <= run <= 65535)
@@ -436,7 +437,7 @@ cudaError_t launch_rlm_level(const RlmArgs& a, int ksize, bool pairs, int sm_cou
       if ((e = cudaFuncSetAttribute(k_multiselect<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                     (int)ssel)) != cudaSuccess)                                   \
         return e;                                                                                 \
-      k_multiselect<K><<<gsel, kSelThreads, ssel, s>>>(a);                                        \
+      k_multiselect<K><<<gsel, kSelBlockThreads, ssel, s>>>(a);                                        \
       if ((e = cudaGetLastError()) != cudaSuccess) return e;                                      \
     }                                                                                             \
     k_rlm_offsets<<<gdel, 512, sdel, s>>>(a);                                                     \
