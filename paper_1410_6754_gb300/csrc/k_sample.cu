@@ -151,13 +151,17 @@ __global__ void __launch_bounds__(512) k_sample_sort(LevelArgs a, K* raw_out, co
 // Unit (i, c) of one segment: row tile i against the column tiles j != i of group c
 // (kRankCols of them).  Every element v of sorted tile i gets, summed over those j,
 // the number of elements of tile j that precede it in the (key, slot) order, i.e.
-// #{y < v} if j > i (later slots) and #{y <= v} if j < i (earlier slots); the row's
-// elements stay in registers across the group's columns and are added to their rank
-// with one atomic each.
+// #{y < v} if j > i (later slots) and #{y <= v} if j < i (earlier slots).  Both
+// tiles are in shared memory and the counts come from merging them: thread t emits
+// outputs [t K, (t+1) K) of the merge (K = (|i| + |j|) / threads), finding where its
+// stretch starts by one binary search along its diagonal (merge path), then merging
+// K steps; an element of tile i emitted after b elements of tile j has count b.
 template <typename K>
 __global__ void __launch_bounds__(512) k_cross_rank(LevelArgs a) {
-  constexpr int NT = 512, EPT = kSampleTile / NT;
-  __shared__ K tile_s[kSampleTile];
+  constexpr int NT = 512;
+  __shared__ K ta[kSampleTile];
+  __shared__ K tb[kSampleTile];
+  __shared__ uint32_t acc[kSampleTile];
   const uint32_t nseg = a.ctr->nseg;
   const uint32_t units = a.ctr->pairs;
   const K* samp = (const K*)a.sample;
@@ -167,45 +171,50 @@ __global__ void __launch_bounds__(512) k_cross_rank(LevelArgs a) {
     const uint32_t ngroups = (si.T - 1 + kRankCols - 1) / kRankCols;
     const uint32_t q = p - si.pair_off;
     const uint32_t i = q / ngroups, c = q % ngroups;
-    const uint32_t ci = min((uint32_t)kSampleTile, si.S - i * kSampleTile);
+    const uint32_t ca = min((uint32_t)kSampleTile, si.S - i * kSampleTile);
     const K* ti = samp + si.samp_off + i * kSampleTile;
-    K v[EPT];
-    uint32_t acc[EPT];
-#pragma unroll
-    for (int u = 0; u < EPT; ++u) {
-      const uint32_t e = threadIdx.x + u * NT;
-      v[u] = e < ci ? ti[e] : K(0);
-      acc[u] = 0;
+    __syncthreads();  // (the previous unit is done with the shared arrays)
+    for (uint32_t e = threadIdx.x; e < ca; e += NT) {
+      ta[e] = ti[e];
+      acc[e] = 0;
     }
     const uint32_t jj_end = min((c + 1) * kRankCols, si.T - 1);
     for (uint32_t jj = c * kRankCols; jj < jj_end; ++jj) {
       const uint32_t j = jj < i ? jj : jj + 1;
-      const uint32_t cj = min((uint32_t)kSampleTile, si.S - j * kSampleTile);
+      const uint32_t cb = min((uint32_t)kSampleTile, si.S - j * kSampleTile);
       const K* tj = samp + si.samp_off + j * kSampleTile;
-      __syncthreads();  // (the previous column's searches are done)
-      for (uint32_t e = threadIdx.x; e < cj; e += NT) tile_s[e] = tj[e];
+      __syncthreads();  // (the previous column's merge is done with tb)
+      for (uint32_t e = threadIdx.x; e < cb; e += NT) tb[e] = tj[e];
       __syncthreads();
-      const bool inclusive = j < i;
-#pragma unroll
-      for (int u = 0; u < EPT; ++u) {
-        if (threadIdx.x + u * NT < ci) {
-          uint32_t lo = 0, hi = cj;  // first position whose key is > v (inclusive) / >= v
-          while (lo < hi) {
-            const uint32_t mid = (lo + hi) >> 1;
-            const K y = tile_s[mid];
-            const bool before = inclusive ? (y <= v[u]) : (y < v[u]);
-            if (before) lo = mid + 1; else hi = mid;
+      // y of tile j precedes x of tile i: y <= x when j < i, y < x otherwise
+      const bool incl = j < i;
+      auto b_first = [&](K y, K x) { return incl ? y <= x : y < x; };
+      const uint32_t total = ca + cb;
+      const uint32_t per = (total + NT - 1) / NT;
+      const uint32_t d0 = min(threadIdx.x * per, total), d1 = min(d0 + per, total);
+      if (d0 < d1) {
+        // x = tile-i elements among the first d0 outputs: the smallest x for which
+        // tb[d0 - 1 - x] precedes ta[x] (that predicate only turns from false to true
+        // as x grows)
+        uint32_t lo = d0 > cb ? d0 - cb : 0u, hi = min(d0, ca);
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (b_first(tb[d0 - 1 - mid], ta[mid])) hi = mid; else lo = mid + 1;
+        }
+        uint32_t x = lo, y = d0 - lo;
+        for (uint32_t d = d0; d < d1; ++d) {
+          if (y >= cb || (x < ca && !b_first(tb[y], ta[x]))) {
+            acc[x] += y;
+            ++x;
+          } else {
+            ++y;
           }
-          acc[u] += lo;
         }
       }
     }
-#pragma unroll
-    for (int u = 0; u < EPT; ++u) {
-      const uint32_t e = threadIdx.x + u * NT;
-      if (e < ci && acc[u]) atomicAdd(&a.srank[si.samp_off + i * kSampleTile + e], acc[u]);
-    }
     __syncthreads();
+    for (uint32_t e = threadIdx.x; e < ca; e += NT)
+      if (acc[e]) atomicAdd(&a.srank[si.samp_off + i * kSampleTile + e], acc[e]);
   }
 }
 
