@@ -162,15 +162,26 @@ __device__ __forceinline__ void load_item(const K* src, uint32_t b, uint32_t m, 
   }
 }
 
+// Cells of an item of m keys: 2m rounded up to 8 (whole 128-bit words of counters),
+// at most CELLS.
+template <typename K, bool PAIRS>
+__device__ __forceinline__ uint32_t item_cells(uint32_t m) {
+  return min(BaseCfg<K, PAIRS>::CELLS, max(8u, (2 * m + 7) & ~7u));
+}
+
 // Sorts the item whose keys are already in x (load_item) and writes it to dst[b, b+m);
 // payloads are read from vsrc here.  next() is called once the keys in x are no
 // longer needed (it may load the block's next item into x, whose load latency then
 // overlaps this item's ranking); src and dst may be the same buffer, and the next
-// item never overlaps this one.
+// item never overlaps this one.  precleared: the counters and flags of this item are
+// already zero.  next_m > 0: the usual path clears the counters and flags of a next
+// item of next_m keys while it copies this one out (no barrier of its own) and
+// returns true; every other path returns false.
 template <typename K, bool PAIRS, typename Next>
-__device__ __forceinline__ void sort_loaded(K (&x)[BaseCfg<K, PAIRS>::KPT], K* dst, const uint64_t* vsrc,
+__device__ __forceinline__ bool sort_loaded(K (&x)[BaseCfg<K, PAIRS>::KPT], K* dst, const uint64_t* vsrc,
                                             uint64_t* vdst, uint32_t b, uint32_t m, int tf_out,
-                                            const BaseSmem<K>& sm, Next next) {
+                                            const BaseSmem<K>& sm, Next next, uint32_t next_m = 0,
+                                            bool precleared = false) {
   using C = BaseCfg<K, PAIRS>;
   constexpr int NT = C::NT, KPT = C::KPT, NW = NT / 32;
   const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -251,10 +262,9 @@ __device__ __forceinline__ void sort_loaded(K (&x)[BaseCfg<K, PAIRS>::KPT], K* d
       }
     }
     next();
-    return;
+    return false;
   }
-  // cells: M = 2m rounded up to 8 (whole 128-bit words of counters), at most CELLS
-  const uint32_t M = min(C::CELLS, max(8u, (2 * m + 7) & ~7u));
+  const uint32_t M = item_cells<K, PAIRS>(m);
   const K range = (K)(kmax - kmin);
   const int nb = bitlen<K>(range);
   const uint32_t sh = nb > 32 ? (uint32_t)(nb - 32) : 0u;
@@ -265,9 +275,11 @@ __device__ __forceinline__ void sort_loaded(K (&x)[BaseCfg<K, PAIRS>::KPT], K* d
   const uint32_t scale = (uint32_t)fminf(fs, 4294967040.0f);
   const CellMap<K> cell{kmin, sh, scale};
   const uint32_t nv = M / 8;  // 128-bit words of counters
-  for (uint32_t i = tid; i < nv; i += NT) ((uint4*)sm.cw)[i] = make_uint4(0, 0, 0, 0);
-  if (tid == 0) sm.flag[0] = sm.flag[1] = sm.flag[2] = 0;
-  __syncthreads();
+  if (!precleared) {
+    for (uint32_t i = tid; i < nv; i += NT) ((uint4*)sm.cw)[i] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) sm.flag[0] = sm.flag[1] = sm.flag[2] = 0;
+    __syncthreads();
+  }
   // count the cells; the count a key's atomic returns is its arrival rank in its cell
   uint32_t rr[(KPT + 1) / 2];  // ranks, 16 bits per key
 #pragma unroll
@@ -301,8 +313,20 @@ __device__ __forceinline__ void sort_loaded(K (&x)[BaseCfg<K, PAIRS>::KPT], K* d
       mx = __vmaxu2(mx, __vmaxu2(__vmaxu2(v.x, v.y), __vmaxu2(v.z, v.w)));
     }
     if (max(mx & 0xFFFFu, mx >> 16) > C::BIGCELL) sm.flag[0] = 1;
-    uint32_t total;
-    uint32_t run = block_exclusive_scan<NT, uint32_t>(t, ws, total);  // (barriers)
+    // exclusive prefix of t over the block with one barrier: warp scans, then every
+    // thread adds the totals of the warps before its own (ws is next written after
+    // the barriers below)
+    uint32_t inc = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if (lane >= (uint32_t)o) inc += y;
+    }
+    if (lane == 31) ws[w] = inc;
+    __syncthreads();
+    uint32_t run = inc - t;
+#pragma unroll
+    for (int j = 0; j < NW; ++j) run += j < (int)w ? ws[j] : 0u;
     auto pre = [&](uint32_t u) {  // word (lo, hi) -> (run, run + lo)
       const uint32_t o = run * 0x10001u + (u << 16);
       run += (u * 0x10001u) >> 16;
@@ -361,7 +385,7 @@ __device__ __forceinline__ void sort_loaded(K (&x)[BaseCfg<K, PAIRS>::KPT], K* d
       // uniform over [min, max]: ranks in cells would cost the square of the cell
       // size): bitonic sort of the item, whose cost does not depend on the keys.
       bitonic_block<K, PAIRS>(dst, vdst, b, m, tf_out, sm);
-      return;
+      return false;
     }
   }
   if (!big && sm.flag[2] <= C::LIST) {
@@ -391,11 +415,17 @@ __device__ __forceinline__ void sort_loaded(K (&x)[BaseCfg<K, PAIRS>::KPT], K* d
       }
     }
     __syncthreads();
+    // the counters and flags are free now: clear them for the next item on the way
+    if (next_m) {
+      const uint32_t nvn = item_cells<K, PAIRS>(next_m) / 8;
+      for (uint32_t i = tid; i < nvn; i += NT) ((uint4*)sm.cw)[i] = make_uint4(0, 0, 0, 0);
+      if (tid == 0) sm.flag[0] = sm.flag[1] = sm.flag[2] = 0;
+    }
     for (uint32_t i = tid; i < m; i += NT) {
       dst[b + i] = order_out<K>(sm.keys[i], tf_out);
       if constexpr (PAIRS) vdst[b + i] = sm.vals[sm.pos[i]];
     }
-    return;
+    return next_m != 0;
   }
   auto rank_all = [&](auto one_value_check) {
     for (uint32_t s = tid; s < m; s += NT) {
@@ -445,6 +475,7 @@ __device__ __forceinline__ void sort_loaded(K (&x)[BaseCfg<K, PAIRS>::KPT], K* d
   } else {
     rank_all([](uint32_t, uint32_t) { return false; });
   }
+  return false;
 }
 
 // One item on its own (no prefetch).
@@ -522,6 +553,7 @@ __global__ void __launch_bounds__(512, BaseCfg<K, PAIRS>::MINB) k_basecase(BaseA
   BcItem item = blockIdx.x < nitems ? a.items[blockIdx.x] : none;
   K x[C::KPT];
   if (sortable(item)) load_item<K, PAIRS>(src, item.begin, item.end - item.begin, a.tf_load, x);
+  bool precleared = false;  // (block-uniform) the counters are zero for this item
   for (uint32_t it = blockIdx.x; it < nitems; it += gridDim.x) {
     const BcItem nxt = it + gridDim.x < nitems ? a.items[it + gridDim.x] : none;
     if (threadIdx.x == 0 && sortable(nxt)) {  // the next item's keys (and payloads) into L2 now
@@ -539,7 +571,8 @@ __global__ void __launch_bounds__(512, BaseCfg<K, PAIRS>::MINB) k_basecase(BaseA
       }
       prefetch();
     } else if (m <= C::CAP) {
-      sort_loaded<K, PAIRS>(x, out, a.vsrc, a.vout, b, m, a.tf_store, sm, prefetch);
+      precleared = sort_loaded<K, PAIRS>(x, out, a.vsrc, a.vout, b, m, a.tf_store, sm, prefetch,
+                                         sortable(nxt) ? nxt.end - nxt.begin : 0u, precleared);
     } else {
       prefetch();
     }
