@@ -169,8 +169,11 @@ def run_reference(args, wl):
     O.sort_keys(wl["kt"], probe)
     per_key = (time.perf_counter() - t0) / len(probe)
     budget = 120.0 / max(1, args.steps + args.warmup)
-    m = int(min(full, max(1 << 16, budget / max(per_key, 1e-12))))
-    m = 1 << (m.bit_length() - 1)
+    # the probe's cost per key grows with log2 of the size: halve m until
+    # m * per_key * log2(m) / 18 fits the per-step budget
+    m = 1 << (int(min(full, max(1 << 16, budget / max(per_key, 1e-12)))).bit_length() - 1)
+    while m > (1 << 16) and m * per_key * (m.bit_length() - 1) / 18.0 > budget:
+        m >>= 1
     sample = I.generate(wl["dist"], m, 0, wl["bits"])
     for _ in range(args.warmup):
         O.sort_keys(wl["kt"], sample)
