@@ -15,6 +15,8 @@
 //       every tile between cuts j and j+1 goes, in tile order, to new part j.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "cta_utils.cuh"
 #include "rlm.cuh"
 
@@ -180,6 +182,175 @@ __global__ void __launch_bounds__(kSelBlockThreads) k_multiselect(RlmArgs a) {
     uint32_t* row = a.cuts + ((size_t)part * (a.r + 1) + j) * a.max_tiles;
     for (uint32_t t = tid; t < T; t += NT) row[t] = wlo[t];
     __syncthreads();
+  }
+}
+
+// The same selection by a cluster of kSelCluster blocks, for levels with fewer
+// selections than SMs (one block per selection would leave most of the GPU idle while
+// every block walks all the part's tiles): block c of the cluster keeps the windows
+// of tiles [c tpc, (c+1) tpc); window sums, the pivot and the counts before it are
+// exchanged through distributed shared memory with three cluster barriers per round.
+// Elements are numbered in (block, thread, tile) order; the pivot rule and the
+// take / shrink rule are those of the block version.
+constexpr int kSelCluster = 8;
+
+template <typename K>
+__global__ void __cluster_dims__(kSelCluster, 1, 1) __launch_bounds__(kSelBlockThreads)
+    k_multiselect_cluster(RlmArgs a, uint32_t tpc) {
+  namespace cg = cooperative_groups;
+  constexpr int NT = kSelBlockThreads, CS = kSelCluster;
+  constexpr int G = 4;  // binary searches of one thread interleaved
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint16_t* wlo = (uint16_t*)smem;  // windows of this block's tiles
+  uint16_t* whi = wlo + tpc;
+  uint16_t* wcnt = whi + tpc;
+  __shared__ uint32_t ws[NT / 32 + 1];
+  __shared__ uint32_t pub_w, pub_t, pub_c;  // published: window total, taken, count before pivot
+  __shared__ unsigned long long pub_key;    // published by the block holding the pivot
+  __shared__ uint32_t pub_tile, pub_pos;
+  __shared__ uint32_t arr_w[CS], arr_t[CS], arr_c[CS];
+  __shared__ unsigned long long piv_key;
+  __shared__ uint32_t piv_tile, piv_pos;
+  const uint32_t tid = threadIdx.x, crank = cluster.block_rank();
+  const uint32_t per_part = a.r - 1;
+  const K* keys = (const K*)a.src;
+  const uint32_t nclusters = gridDim.x / CS;
+  for (uint32_t job = blockIdx.x / CS; job < a.nparts * per_part; job += nclusters) {
+    const uint32_t part = job / per_part, j = job % per_part + 1;  // cut j of the part
+    const uint32_t plo = a.part_lo[part], m = a.part_lo[part + 1] - plo;
+    const uint32_t T = (m + a.run - 1) / a.run;
+    const uint32_t k = (uint32_t)(((uint64_t)j * m) / a.r);
+    const uint32_t t_lo = min(crank * tpc, T), nt = min(t_lo + tpc, T) - t_lo;  // this block's tiles
+    for (uint32_t lt = tid; lt < nt; lt += NT) {
+      wlo[lt] = 0;
+      whi[lt] = (uint16_t)min(a.run, m - (t_lo + lt) * a.run);
+    }
+    uint64_t state = rlm_mix(a.seed + (uint64_t)(a.level + 1) * 0x9E3779B97F4A7C15ull);
+    state = rlm_mix(state + (((uint64_t)part << 32) | j));
+    __syncthreads();
+    PivotRule rule;
+    for (uint32_t round = 0;; ++round) {
+      uint32_t wsum = 0, taken = 0;
+      for (uint32_t lt = tid; lt < nt; lt += NT) {
+        wsum += whi[lt] - wlo[lt];
+        taken += wlo[lt];
+      }
+      uint32_t wblk, tblk;
+      const uint32_t wpre = block_exclusive_scan<NT, uint32_t>(wsum, ws, wblk);
+      block_exclusive_scan<NT, uint32_t>(taken, ws, tblk);
+      if (tid == 0) {
+        pub_w = wblk;
+        pub_t = tblk;
+      }
+      cluster.sync();  // (1) window totals published
+      if (tid < CS) {
+        arr_w[tid] = *cluster.map_shared_rank(&pub_w, tid);
+        arr_t[tid] = *cluster.map_shared_rank(&pub_t, tid);
+      }
+      __syncthreads();
+      uint32_t total = 0, taken_all = 0, base = 0;
+#pragma unroll
+      for (int c = 0; c < CS; ++c) {
+        total += arr_w[c];
+        taken_all += arr_t[c];
+        base += (uint32_t)c < crank ? arr_w[c] : 0u;
+      }
+      if (taken_all == k) break;  // (the same in every block of the cluster)
+      if (total == 0 || round == kSelMaxRounds) {  // cannot happen on consistent input
+        if (tid == 0 && crank == 0) atomicOr(a.status, ST_OVERFLOW);
+        break;
+      }
+      const bool targeted = rule.next(total);
+      state += 0x9E3779B97F4A7C15ull;
+      const uint32_t u = (uint32_t)__umul64hi(rlm_mix(state), (uint64_t)total);
+      uint32_t owner = 0;
+      {
+        uint32_t b = 0;
+#pragma unroll
+        for (int c = 0; c < CS; ++c) {
+          if (u >= b && u < b + arr_w[c]) owner = c;
+          b += arr_w[c];
+        }
+      }
+      if (crank == owner && u - base >= wpre && u - base < wpre + wsum) {
+        uint32_t rem = u - base - wpre;
+        for (uint32_t lt = tid; lt < nt; lt += NT) {
+          const uint32_t len = whi[lt] - wlo[lt];
+          if (rem < len) {
+            const uint32_t pos = wlo[lt] + pivot_pos(targeted, rem, len, k - taken_all, total);
+            pub_key = (unsigned long long)keys[plo + (t_lo + lt) * a.run + pos];
+            pub_tile = t_lo + lt;
+            pub_pos = pos;
+            break;
+          }
+          rem -= len;
+        }
+      }
+      cluster.sync();  // (2) pivot published
+      if (tid == 0) {
+        piv_key = *cluster.map_shared_rank(&pub_key, owner);
+        piv_tile = *cluster.map_shared_rank(&pub_tile, owner);
+        piv_pos = *cluster.map_shared_rank(&pub_pos, owner);
+      }
+      __syncthreads();
+      const K pk = (K)piv_key;
+      const uint32_t pt = piv_tile, pp = piv_pos;
+      uint32_t cnt = 0;
+      for (uint32_t l0 = tid; l0 < nt; l0 += NT * G) {
+        uint32_t lo[G], hi[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const uint32_t lt = l0 + g * NT;
+          lo[g] = hi[g] = 0;
+          if (lt < nt) {
+            lo[g] = wlo[lt];
+            hi[g] = whi[lt];
+            if (t_lo + lt == pt) lo[g] = hi[g] = min(max(pp, lo[g]), hi[g]);
+          }
+        }
+        for (;;) {
+          bool active = false;
+#pragma unroll
+          for (int g = 0; g < G; ++g) {
+            if (lo[g] < hi[g]) {
+              const uint32_t t = t_lo + l0 + g * NT;
+              const uint32_t mid = (lo[g] + hi[g]) >> 1;
+              const K v = keys[plo + t * a.run + mid];
+              if (t < pt ? v <= pk : v < pk) lo[g] = mid + 1; else hi[g] = mid;
+              active = true;
+            }
+          }
+          if (!active) break;
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const uint32_t lt = l0 + g * NT;
+          if (lt < nt) {
+            wcnt[lt] = (uint16_t)lo[g];
+            cnt += lo[g];
+          }
+        }
+      }
+      uint32_t cblk;
+      block_exclusive_scan<NT, uint32_t>(cnt, ws, cblk);
+      if (tid == 0) pub_c = cblk;
+      cluster.sync();  // (3) counts published
+      if (tid < CS) arr_c[tid] = *cluster.map_shared_rank(&pub_c, tid);
+      __syncthreads();
+      uint32_t before_all = 0;
+#pragma unroll
+      for (int c = 0; c < CS; ++c) before_all += arr_c[c];
+      const bool take = before_all < k;  // the pivot and all before it are among the first k
+      for (uint32_t lt = tid; lt < nt; lt += NT) {
+        if (take) wlo[lt] = (uint16_t)(t_lo + lt == pt ? pp + 1 : wcnt[lt]);
+        else whi[lt] = wcnt[lt];
+      }
+      __syncthreads();
+    }
+    uint32_t* row = a.cuts + ((size_t)part * (a.r + 1) + j) * a.max_tiles;
+    for (uint32_t lt = tid; lt < nt; lt += NT) row[t_lo + lt] = wlo[lt];
+    cluster.sync();  // (no block reuses the published values of this job before all have read them)
   }
 }
 
@@ -421,6 +592,11 @@ cudaError_t launch_rlm_level(const RlmArgs& a, int ksize, bool pairs, int sm_cou
   const size_t ssel = rlm_select_smem(a.max_tiles), sdel = rlm_deliver_smem(a.max_tiles);
   const int gsel = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)a.nparts * (a.r - 1), (uint64_t)sm_count * 8));
   const int gdel = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)a.nparts * a.r, (uint64_t)sm_count * 8));
+  const uint64_t sel_jobs = (uint64_t)a.nparts * (a.r - 1);
+  const uint32_t tpc = (a.max_tiles + kSelCluster - 1) / kSelCluster;
+  const size_t sclu = (size_t)tpc * 6 + 16;
+  const int gclu = (int)std::max<uint64_t>(1, std::min<uint64_t>(sel_jobs, (uint64_t)sm_count * 2 / kSelCluster)) *
+                   kSelCluster;
   const uint64_t copy_tasks = (uint64_t)a.nparts * a.r * ((a.max_tiles + 31) / 32);
   const int gcopy = (int)std::max<uint64_t>(1, std::min<uint64_t>((copy_tasks + 7) / 8, (uint64_t)sm_count * 8));
   if ((e = cudaFuncSetAttribute(k_rlm_offsets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sdel)) !=
@@ -430,14 +606,21 @@ cudaError_t launch_rlm_level(const RlmArgs& a, int ksize, bool pairs, int sm_cou
   const int gselw = (int)std::max<uint64_t>(1, std::min<uint64_t>(wjobs, (uint64_t)sm_count * 4));
 #define AMS_RLM_LAUNCH(K, P)                                                                      \
   do {                                                                                            \
-    if (a.r > 1 && a.max_tiles <= kWarpTiles) {                                                   \
+    bool selected = a.r <= 1; /* one part per part: nothing to select */                         \
+    if (!selected && a.max_tiles <= kWarpTiles) {                                                 \
       k_multiselect_warp<K><<<gselw, kSelThreads, 0, s>>>(a);                                     \
       if ((e = cudaGetLastError()) != cudaSuccess) return e;                                      \
-    } else if (a.r > 1) {                                                                         \
+      selected = true;                                                                            \
+    }                                                                                             \
+    if (!selected && sel_jobs < (uint64_t)sm_count) {                                             \
+      k_multiselect_cluster<K><<<gclu, kSelBlockThreads, sclu, s>>>(a, tpc);                      \
+      selected = cudaGetLastError() == cudaSuccess; /* a refused cluster launch: blocks */        \
+    }                                                                                             \
+    if (!selected) {                                                                              \
       if ((e = cudaFuncSetAttribute(k_multiselect<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                     (int)ssel)) != cudaSuccess)                                   \
         return e;                                                                                 \
-      k_multiselect<K><<<gsel, kSelBlockThreads, ssel, s>>>(a);                                        \
+      k_multiselect<K><<<gsel, kSelBlockThreads, ssel, s>>>(a);                                   \
       if ((e = cudaGetLastError()) != cudaSuccess) return e;                                      \
     }                                                                                             \
     k_rlm_offsets<<<gdel, 512, sdel, s>>>(a);                                                     \

@@ -59,6 +59,28 @@ def test_rlm_shapes_in_place(n, run, parts):
     assert np.array_equal(to_np(dv, np.uint64), want[1])
 
 
+@pytest.mark.parametrize("kt,bits", [(O.KT_U32, 32), (O.KT_U64, 64), (O.KT_F32, 32)])
+@pytest.mark.parametrize("pairs", [False, True])
+def test_rlm_wide_first_level(kt, bits, pairs):
+    """Few selections over many tiles (7 over 2049 tiles: the cluster selection), then
+    many over about 257 tiles each (one block per selection)."""
+    n, run, parts = (1 << 21) + 1234, 1024, [8, 300]
+    keys = _keys(kt, bits, "uniform", n, 11)
+    vals = np.arange(n, dtype=np.uint64)
+    kin = to_dev(keys)
+    kout = torch.empty_like(kin)
+    vin = to_dev(vals) if pairs else None
+    vout = torch.empty_like(vin) if pairs else None
+    ams.rlm_sort(kin, kout, vin, vout, run=run, parts=parts, seed=5, kt=kt)
+    ams.sync()
+    if pairs:
+        ek, ev = O.sort_pairs(kt, keys, vals)
+        assert np.array_equal(to_np(vout, np.uint64), ev)
+    else:
+        ek = O.sort_keys(kt, keys)
+    assert same_bits(to_np(kout, keys.dtype), ek)
+
+
 def test_rlm_rejects_unfinished_parts():
     # the last level's parts must fit one tile
     k = torch.zeros(10000, dtype=torch.int64, device="cuda")
