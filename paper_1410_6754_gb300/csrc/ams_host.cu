@@ -441,19 +441,23 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
     la.r = lp.r;
     la.CH = lp.CH;
     la.last = l == p.L;
+    // Delivery targets alternate between the output and the temporary buffer.  An
+    // out-of-place sort (keys and payloads) delivers level 1 straight into the output,
+    // so that the pieces a level-1 delivery already finalises (equality buckets of
+    // duplicate-heavy input) need no copy; an in-place sort must deliver level 1 into
+    // the temporary buffer, since the output is its input.
+    const bool out_of_place = !inplace && (!rq->vals_in || rq->vals_in != rq->vals_out);
+    auto to_out = [&](int lv) { return ((lv % 2) == 1) == out_of_place; };
+    la.dst = to_out(l) ? rq->keys_out : b.tmp;
+    la.vdst = to_out(l) ? rq->vals_out : b.vtmp;
     if (l == 1) {
       la.src = rq->keys_in;
       la.vsrc = rq->vals_in;
-      la.dst = b.tmp;
-      la.vdst = b.vtmp;
       la.tf_src = f32 ? 1 : 0;
       la.segs = b.segs1;
     } else {
-      const bool even = (l % 2) == 0;
-      la.src = even ? b.tmp : rq->keys_out;
-      la.vsrc = even ? b.vtmp : rq->vals_out;
-      la.dst = even ? rq->keys_out : b.tmp;
-      la.vdst = even ? rq->vals_out : b.vtmp;
+      la.src = to_out(l - 1) ? rq->keys_out : b.tmp;
+      la.vsrc = to_out(l - 1) ? rq->vals_out : b.vtmp;
       la.tf_src = 0;
       la.segs = b.lv[l - 2].segs_next;
     }
