@@ -30,6 +30,7 @@ struct Plan {
   uint32_t b = 0, a_fixed = 0, C = 0;
   int ksize = 8;
   bool pairs = false;
+  bool small = false;  // pairs base case of half the capacity (C <= its capacity)
   uint64_t n = 0, nseg_user = 1;
   uint64_t seg1_cap = 0, bc0_cap = 0, big_cap = 0, tiny_cap = 0;
   LevelPlan lv[kMaxLevels];
@@ -68,6 +69,11 @@ ams_status make_plan(uint64_t n, uint64_t nseg_user, ams_key_type kt, bool pairs
     est = (est + rr.back() - 1) / rr.back();
   }
   p->L = (int)rr.size();
+  // a pairs sort of one segment whose leaves are expected to fit the base case of
+  // half the capacity (with 25% slack for uneven groups) uses it: two blocks per SM
+  if (pairs && !o.basecase_cap && nseg_user == 1 && est * 5 / 4 <= basecase_small_cap())
+    p->C = basecase_small_cap();
+  p->small = pairs && p->C <= basecase_small_cap();
   // every segment holds at most C keys: level 0 hands them all to the base case and
   // the distribution levels would find no work, so none is launched
   if (n <= p->C) p->L = 0;
@@ -403,7 +409,7 @@ static ams_status run_sort(Context* cx, const ams_request* rq, cudaStream_t s) {
     ba.status = b.status;
     const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(cap_items, bc_grid_cap));
     ln.begin(AMS_K_BASECASE);
-    cudaError_t e = ln.end(launch_basecase(ba, p.ksize, p.pairs, big, grid, s));
+    cudaError_t e = ln.end(launch_basecase(ba, p.ksize, p.pairs, big, grid, s, p.small));
     return cuda_status(e);
   };
   // no offsets and n above C: one segment [0, n) that level 0 hands to level 1, so

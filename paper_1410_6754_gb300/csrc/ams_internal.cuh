@@ -218,7 +218,9 @@ cudaError_t launch_scan(const LevelArgs& a, int grid, bool few_segments, cudaStr
 cudaError_t launch_binpack(const LevelArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_scatter(const LevelArgs& a, int ksize, bool pairs, bool stable, int grid,
                            cudaStream_t s);
-cudaError_t launch_basecase(const BaseArgs& a, int ksize, bool pairs, bool big, int grid, cudaStream_t s);
+// small: the pairs base case of half the capacity (two blocks per SM)
+cudaError_t launch_basecase(const BaseArgs& a, int ksize, bool pairs, bool big, int grid, cudaStream_t s,
+                            bool small = false);
 cudaError_t launch_tiny(const BaseArgs& a, int ksize, bool pairs, int grid, cudaStream_t s);
 struct RlmArgs;
 cudaError_t launch_rlm_level(const RlmArgs& a, int ksize, bool pairs, int sm_count, cudaStream_t s);
@@ -226,7 +228,8 @@ cudaError_t launch_rlm_level(const RlmArgs& a, int ksize, bool pairs, int sm_cou
 // shared-memory bytes each kernel needs (for occupancy and opt-in)
 size_t scatter_smem_bytes(int ksize, bool pairs, bool stable, uint32_t B);
 size_t classify_smem_bytes(int ksize, uint32_t B, bool tree);
-size_t basecase_smem_bytes(int ksize, bool pairs);
+size_t basecase_smem_bytes(int ksize, bool pairs, bool small = false);
 uint32_t basecase_max_cap(int ksize, bool pairs);
+uint32_t basecase_small_cap();  // capacity of the small pairs base case
 
 }  // namespace ams

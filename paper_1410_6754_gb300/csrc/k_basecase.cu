@@ -15,17 +15,19 @@
 
 namespace ams {
 
-template <typename K, bool PAIRS>
+template <typename K, bool PAIRS, bool SMALL = false>
 struct BaseCfg {
   static constexpr int NT = 512;
-  static constexpr uint32_t CAP = (sizeof(K) == 4 && !PAIRS) ? 16384u : 8192u;
+  // SMALL (pairs only): half the capacity, so that two blocks fit per SM; used when a
+  // sort's leaves are expected to fit it
+  static constexpr uint32_t CAP = SMALL ? 4096u : (sizeof(K) == 4 && !PAIRS) ? 16384u : 8192u;
   static constexpr int KPT = CAP / NT;
   static constexpr uint32_t CELLS = 16384;  // 16-bit counters, two per word
   static constexpr uint32_t BIGCELL = 8;    // cells above this size are checked for one value
   static constexpr uint32_t SKEWCELL = 32;  // a cell above this size with two values: bitonic
   static constexpr uint32_t LIST = CAP / 4;  // cells of two or more keys listed (else ranked per slot)
   // two blocks per SM when their shared memory fits (keys only)
-  static constexpr int MINB = PAIRS ? 1 : 2;
+  static constexpr int MINB = (PAIRS && !SMALL) ? 1 : 2;
 };
 
 template <typename K>
@@ -41,9 +43,9 @@ struct BaseSmem {
   uint16_t* shared;  // cells holding two or more keys (at most LIST)
 };
 
-template <typename K, bool PAIRS>
+template <typename K, bool PAIRS, bool SMALL = false>
 __host__ __device__ constexpr size_t base_smem_layout(size_t* off) {
-  using C = BaseCfg<K, PAIRS>;
+  using C = BaseCfg<K, PAIRS, SMALL>;
   size_t o = 0;
   off[0] = o; o += (size_t)C::CAP * sizeof(K);                          // keys
   off[1] = o; o += (size_t)C::CELLS * 2 + 16;                           // cells (+ end)
@@ -57,10 +59,10 @@ __host__ __device__ constexpr size_t base_smem_layout(size_t* off) {
   return o;
 }
 
-template <typename K, bool PAIRS>
+template <typename K, bool PAIRS, bool SMALL = false>
 __device__ __forceinline__ BaseSmem<K> base_smem(unsigned char* smem) {
   size_t off[8];
-  base_smem_layout<K, PAIRS>(off);
+  base_smem_layout<K, PAIRS, SMALL>(off);
   return BaseSmem<K>{(K*)(smem + off[0]), (uint32_t*)(smem + off[1]), (uint16_t*)(smem + off[2]),
                      (uint64_t*)(smem + off[3]), (K*)(smem + off[4]), (uint32_t*)(smem + off[5]),
                      (uint32_t*)(smem + off[6]), (uint16_t*)(smem + off[7])};
@@ -95,10 +97,10 @@ struct CellMap {
 // Bitonic sort of the m keys in sm.keys[0, m) (pairs: with their input indices in
 // sm.pos, the tiebreak, so the order stays stable), padded with the largest key to
 // the next power of two, then written to dst[b, b+m) (payloads from sm.vals).
-template <typename K, bool PAIRS>
+template <typename K, bool PAIRS, bool SMALL = false>
 __device__ void bitonic_block(K* dst, uint64_t* vdst, uint32_t b, uint32_t m, int tf_out,
                               const BaseSmem<K>& sm) {
-  using C = BaseCfg<K, PAIRS>;
+  using C = BaseCfg<K, PAIRS, SMALL>;
   constexpr int NT = C::NT;
   const uint32_t tid = threadIdx.x;
   uint32_t mp = 1;
@@ -150,10 +152,10 @@ __device__ void bitonic_block(K* dst, uint64_t* vdst, uint32_t b, uint32_t m, in
 // hi = max << 32 | 2^32-1) when those span at least 2^12 values -- the range is then
 // overstated by less than 0.1% -- and from the full keys otherwise.
 // Keys [b, b+m) of src into registers: element e = threadIdx.x + q*NT goes to x[q].
-template <typename K, bool PAIRS>
+template <typename K, bool PAIRS, bool SMALL = false>
 __device__ __forceinline__ void load_item(const K* src, uint32_t b, uint32_t m, int tf_in,
-                                          K (&x)[BaseCfg<K, PAIRS>::KPT]) {
-  using C = BaseCfg<K, PAIRS>;
+                                          K (&x)[BaseCfg<K, PAIRS, SMALL>::KPT]) {
+  using C = BaseCfg<K, PAIRS, SMALL>;
 #pragma unroll
   for (int q = 0; q < C::KPT; ++q) {
     if ((uint32_t)q * C::NT >= m) break;  // (uniform) the rest of the slots are empty
@@ -164,9 +166,9 @@ __device__ __forceinline__ void load_item(const K* src, uint32_t b, uint32_t m, 
 
 // Cells of an item of m keys: 2m rounded up to 8 (whole 128-bit words of counters),
 // at most CELLS.
-template <typename K, bool PAIRS>
+template <typename K, bool PAIRS, bool SMALL = false>
 __device__ __forceinline__ uint32_t item_cells(uint32_t m) {
-  return min(BaseCfg<K, PAIRS>::CELLS, max(8u, (2 * m + 7) & ~7u));
+  return min(BaseCfg<K, PAIRS, SMALL>::CELLS, max(8u, (2 * m + 7) & ~7u));
 }
 
 // Sorts the item whose keys are already in x (load_item) and writes it to dst[b, b+m);
@@ -177,12 +179,12 @@ __device__ __forceinline__ uint32_t item_cells(uint32_t m) {
 // already zero.  next_m > 0: the usual path clears the counters and flags of a next
 // item of next_m keys while it copies this one out (no barrier of its own) and
 // returns true; every other path returns false.
-template <typename K, bool PAIRS, typename Next>
-__device__ __forceinline__ bool sort_loaded(K (&x)[BaseCfg<K, PAIRS>::KPT], K* dst, const uint64_t* vsrc,
+template <typename K, bool PAIRS, bool SMALL, typename Next>
+__device__ __forceinline__ bool sort_loaded(K (&x)[BaseCfg<K, PAIRS, SMALL>::KPT], K* dst, const uint64_t* vsrc,
                                             uint64_t* vdst, uint32_t b, uint32_t m, int tf_out,
                                             const BaseSmem<K>& sm, Next next, uint32_t next_m = 0,
                                             bool precleared = false) {
-  using C = BaseCfg<K, PAIRS>;
+  using C = BaseCfg<K, PAIRS, SMALL>;
   constexpr int NT = C::NT, KPT = C::KPT, NW = NT / 32;
   const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   if constexpr (PAIRS) {
@@ -264,7 +266,7 @@ __device__ __forceinline__ bool sort_loaded(K (&x)[BaseCfg<K, PAIRS>::KPT], K* d
     next();
     return false;
   }
-  const uint32_t M = item_cells<K, PAIRS>(m);
+  const uint32_t M = item_cells<K, PAIRS, SMALL>(m);
   const K range = (K)(kmax - kmin);
   const int nb = bitlen<K>(range);
   const uint32_t sh = nb > 32 ? (uint32_t)(nb - 32) : 0u;
@@ -384,7 +386,7 @@ __device__ __forceinline__ bool sort_loaded(K (&x)[BaseCfg<K, PAIRS>::KPT], K* d
       // Keys crowded into few cells with several values (a distribution far from
       // uniform over [min, max]: ranks in cells would cost the square of the cell
       // size): bitonic sort of the item, whose cost does not depend on the keys.
-      bitonic_block<K, PAIRS>(dst, vdst, b, m, tf_out, sm);
+      bitonic_block<K, PAIRS, SMALL>(dst, vdst, b, m, tf_out, sm);
       return false;
     }
   }
@@ -417,7 +419,7 @@ __device__ __forceinline__ bool sort_loaded(K (&x)[BaseCfg<K, PAIRS>::KPT], K* d
     __syncthreads();
     // the counters and flags are free now: clear them for the next item on the way
     if (next_m) {
-      const uint32_t nvn = item_cells<K, PAIRS>(next_m) / 8;
+      const uint32_t nvn = item_cells<K, PAIRS, SMALL>(next_m) / 8;
       for (uint32_t i = tid; i < nvn; i += NT) ((uint4*)sm.cw)[i] = make_uint4(0, 0, 0, 0);
       if (tid == 0) sm.flag[0] = sm.flag[1] = sm.flag[2] = 0;
     }
@@ -479,18 +481,18 @@ __device__ __forceinline__ bool sort_loaded(K (&x)[BaseCfg<K, PAIRS>::KPT], K* d
 }
 
 // One item on its own (no prefetch).
-template <typename K, bool PAIRS>
+template <typename K, bool PAIRS, bool SMALL = false>
 __device__ __forceinline__ void sort_block(const K* src, K* dst, const uint64_t* vsrc, uint64_t* vdst,
                                            uint32_t b, uint32_t m, int tf_in, int tf_out,
                                            const BaseSmem<K>& sm) {
-  K x[BaseCfg<K, PAIRS>::KPT];
-  load_item<K, PAIRS>(src, b, m, tf_in, x);
-  sort_loaded<K, PAIRS>(x, dst, vsrc, vdst, b, m, tf_out, sm, [] {});
+  K x[BaseCfg<K, PAIRS, SMALL>::KPT];
+  load_item<K, PAIRS, SMALL>(src, b, m, tf_in, x);
+  sort_loaded<K, PAIRS, SMALL>(x, dst, vsrc, vdst, b, m, tf_out, sm, [] {});
 }
 
-template <typename K, bool PAIRS>
+template <typename K, bool PAIRS, bool SMALL = false>
 __device__ void big_sort(const BaseArgs& a, uint32_t b, uint32_t m, const BaseSmem<K>& sm) {
-  using C = BaseCfg<K, PAIRS>;
+  using C = BaseCfg<K, PAIRS, SMALL>;
   const K* src = (const K*)a.src;
   K* out = (K*)a.out;
   K* scr = (K*)a.scratch;
@@ -504,7 +506,7 @@ __device__ void big_sort(const BaseArgs& a, uint32_t b, uint32_t m, const BaseSm
   for (uint32_t r = 0; r < runs; ++r) {
     const uint32_t rb = b + r * C::CAP;
     const uint32_t rm = min(C::CAP, m - r * C::CAP);
-    sort_block<K, PAIRS>(src, bufA, a.vsrc, vA, rb, rm, a.tf_load, passes == 0 ? a.tf_store : 0, sm);
+    sort_block<K, PAIRS, SMALL>(src, bufA, a.vsrc, vA, rb, rm, a.tf_load, passes == 0 ? a.tf_store : 0, sm);
     __syncthreads();
   }
   K* cur = bufA;
@@ -538,11 +540,11 @@ __device__ void big_sort(const BaseArgs& a, uint32_t b, uint32_t m, const BaseSm
   }
 }
 
-template <typename K, bool PAIRS>
-__global__ void __launch_bounds__(512, BaseCfg<K, PAIRS>::MINB) k_basecase(BaseArgs a) {
-  using C = BaseCfg<K, PAIRS>;
+template <typename K, bool PAIRS, bool SMALL = false>
+__global__ void __launch_bounds__(512, BaseCfg<K, PAIRS, SMALL>::MINB) k_basecase(BaseArgs a) {
+  using C = BaseCfg<K, PAIRS, SMALL>;
   extern __shared__ __align__(16) unsigned char smem[];
-  const BaseSmem<K> sm = base_smem<K, PAIRS>(smem);
+  const BaseSmem<K> sm = base_smem<K, PAIRS, SMALL>(smem);
   const uint32_t nitems = *a.nitems;
   const K* src = (const K*)a.src;
   K* out = (K*)a.out;
@@ -552,7 +554,7 @@ __global__ void __launch_bounds__(512, BaseCfg<K, PAIRS>::MINB) k_basecase(BaseA
   const BcItem none{0, 0, BC_COPY, 0};
   BcItem item = blockIdx.x < nitems ? a.items[blockIdx.x] : none;
   K x[C::KPT];
-  if (sortable(item)) load_item<K, PAIRS>(src, item.begin, item.end - item.begin, a.tf_load, x);
+  if (sortable(item)) load_item<K, PAIRS, SMALL>(src, item.begin, item.end - item.begin, a.tf_load, x);
   bool precleared = false;  // (block-uniform) the counters are zero for this item
   for (uint32_t it = blockIdx.x; it < nitems; it += gridDim.x) {
     const BcItem nxt = it + gridDim.x < nitems ? a.items[it + gridDim.x] : none;
@@ -561,7 +563,7 @@ __global__ void __launch_bounds__(512, BaseCfg<K, PAIRS>::MINB) k_basecase(BaseA
       if constexpr (PAIRS) prefetch_l2(a.vsrc + nxt.begin, (size_t)(nxt.end - nxt.begin) * 8);
     }
     auto prefetch = [&] {
-      if (sortable(nxt)) load_item<K, PAIRS>(src, nxt.begin, nxt.end - nxt.begin, a.tf_load, x);
+      if (sortable(nxt)) load_item<K, PAIRS, SMALL>(src, nxt.begin, nxt.end - nxt.begin, a.tf_load, x);
     };
     const uint32_t b = item.begin, m = item.end - item.begin;
     if (item.kind == BC_COPY) {
@@ -571,7 +573,7 @@ __global__ void __launch_bounds__(512, BaseCfg<K, PAIRS>::MINB) k_basecase(BaseA
       }
       prefetch();
     } else if (m <= C::CAP) {
-      precleared = sort_loaded<K, PAIRS>(x, out, a.vsrc, a.vout, b, m, a.tf_store, sm, prefetch,
+      precleared = sort_loaded<K, PAIRS, SMALL>(x, out, a.vsrc, a.vout, b, m, a.tf_store, sm, prefetch,
                                          sortable(nxt) ? nxt.end - nxt.begin : 0u, precleared);
     } else {
       prefetch();
@@ -583,14 +585,14 @@ __global__ void __launch_bounds__(512, BaseCfg<K, PAIRS>::MINB) k_basecase(BaseA
 
 // Groups still larger than the block capacity after the last level (BC_BIG items,
 // kept in their own list so that the hot kernel above stays small).
-template <typename K, bool PAIRS>
+template <typename K, bool PAIRS, bool SMALL = false>
 __global__ void __launch_bounds__(512) k_bigsort(BaseArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const BaseSmem<K> sm = base_smem<K, PAIRS>(smem);
+  const BaseSmem<K> sm = base_smem<K, PAIRS, SMALL>(smem);
   const uint32_t nitems = *a.nitems;
   for (uint32_t it = blockIdx.x; it < nitems; it += gridDim.x) {
     const BcItem item = a.items[it];
-    big_sort<K, PAIRS>(a, item.begin, item.end - item.begin, sm);
+    big_sort<K, PAIRS, SMALL>(a, item.begin, item.end - item.begin, sm);
     __syncthreads();
   }
 }
@@ -601,7 +603,7 @@ __global__ void __launch_bounds__(512) k_bigsort(BaseArgs a) {
 // (key, index) ordered before it, counted against every element of the segment (read
 // from shared memory, where the whole warp reads one element at a time: a broadcast).
 // Many segments per block, no block barrier.
-template <typename K, bool PAIRS>
+template <typename K, bool PAIRS, bool SMALL = false>
 __global__ void __launch_bounds__(512, 2) k_tiny(BaseArgs a) {
   constexpr int NW = 16, J = kTiny / 32;
   __shared__ K sk[NW][kTiny];
@@ -659,38 +661,48 @@ cudaError_t launch_tiny(const BaseArgs& a, int ksize, bool pairs, int grid, cuda
   return cudaGetLastError();
 }
 
-size_t basecase_smem_bytes(int ksize, bool pairs) {
+size_t basecase_smem_bytes(int ksize, bool pairs, bool small) {
   size_t off[8];
+  if (pairs && small)
+    return ksize == 4 ? base_smem_layout<uint32_t, true, true>(off) : base_smem_layout<uint64_t, true, true>(off);
   if (ksize == 4) return pairs ? base_smem_layout<uint32_t, true>(off) : base_smem_layout<uint32_t, false>(off);
   return pairs ? base_smem_layout<uint64_t, true>(off) : base_smem_layout<uint64_t, false>(off);
 }
+
+uint32_t basecase_small_cap() { return BaseCfg<uint64_t, true, true>::CAP; }
 
 uint32_t basecase_max_cap(int ksize, bool pairs) {
   if (ksize == 4) return pairs ? BaseCfg<uint32_t, true>::CAP : BaseCfg<uint32_t, false>::CAP;
   return pairs ? BaseCfg<uint64_t, true>::CAP : BaseCfg<uint64_t, false>::CAP;
 }
 
-cudaError_t launch_basecase(const BaseArgs& a, int ksize, bool pairs, bool big, int grid, cudaStream_t s) {
-  const size_t sm = basecase_smem_bytes(ksize, pairs);
+cudaError_t launch_basecase(const BaseArgs& a, int ksize, bool pairs, bool big, int grid, cudaStream_t s,
+                            bool small) {
+  small = small && pairs;
+  const size_t sm = basecase_smem_bytes(ksize, pairs, small);
   cudaError_t e;
-#define AMS_LAUNCH_BASE(K, P)                                                                  \
+#define AMS_LAUNCH_BASE(K, P, S)                                                               \
   do {                                                                                         \
     if (big) {                                                                                 \
-      e = cudaFuncSetAttribute(k_bigsort<K, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+      e = cudaFuncSetAttribute(k_bigsort<K, P, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                (int)sm);                                                       \
       if (e != cudaSuccess) return e;                                                          \
-      k_bigsort<K, P><<<grid, 512, sm, s>>>(a);                                                \
+      k_bigsort<K, P, S><<<grid, 512, sm, s>>>(a);                                             \
     } else {                                                                                   \
-      e = cudaFuncSetAttribute(k_basecase<K, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+      e = cudaFuncSetAttribute(k_basecase<K, P, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                (int)sm);                                                       \
       if (e != cudaSuccess) return e;                                                          \
-      k_basecase<K, P><<<grid, 512, sm, s>>>(a);                                               \
+      k_basecase<K, P, S><<<grid, 512, sm, s>>>(a);                                            \
     }                                                                                          \
   } while (0)
   if (ksize == 4) {
-    if (pairs) AMS_LAUNCH_BASE(uint32_t, true); else AMS_LAUNCH_BASE(uint32_t, false);
+    if (small) AMS_LAUNCH_BASE(uint32_t, true, true);
+    else if (pairs) AMS_LAUNCH_BASE(uint32_t, true, false);
+    else AMS_LAUNCH_BASE(uint32_t, false, false);
   } else {
-    if (pairs) AMS_LAUNCH_BASE(uint64_t, true); else AMS_LAUNCH_BASE(uint64_t, false);
+    if (small) AMS_LAUNCH_BASE(uint64_t, true, true);
+    else if (pairs) AMS_LAUNCH_BASE(uint64_t, true, false);
+    else AMS_LAUNCH_BASE(uint64_t, false, false);
   }
 #undef AMS_LAUNCH_BASE
   return cudaGetLastError();
@@ -716,14 +728,14 @@ constexpr uint64_t kNoallocMax = AMS_NOALLOC_MAX_KEYS;
 // keys in the first half (as 64-bit slots), payloads in the second half
 static __device__ __align__(256) uint64_t g_noalloc_scratch[2 * kNoallocMax];
 
-template <typename K, bool PAIRS>
+template <typename K, bool PAIRS, bool SMALL = false>
 __global__ void __launch_bounds__(512) k_sort_noalloc(void* keys, uint64_t* vals, uint32_t n, int tf,
                                                       uint64_t* scratch) {
-  using C = BaseCfg<K, PAIRS>;
+  using C = BaseCfg<K, PAIRS, SMALL>;
   extern __shared__ __align__(16) unsigned char smem[];
-  const BaseSmem<K> sm = base_smem<K, PAIRS>(smem);
+  const BaseSmem<K> sm = base_smem<K, PAIRS, SMALL>(smem);
   if (n <= C::CAP) {
-    sort_block<K, PAIRS>((const K*)keys, (K*)keys, vals, vals, 0, n, tf, tf, sm);
+    sort_block<K, PAIRS, SMALL>((const K*)keys, (K*)keys, vals, vals, 0, n, tf, tf, sm);
     return;
   }
   BaseArgs a{};
@@ -735,7 +747,7 @@ __global__ void __launch_bounds__(512) k_sort_noalloc(void* keys, uint64_t* vals
   a.vscratch = scratch + kNoallocMax;  // payload part
   a.tf_load = tf;
   a.tf_store = tf;
-  big_sort<K, PAIRS>(a, 0, n, sm);
+  big_sort<K, PAIRS, SMALL>(a, 0, n, sm);
 }
 
 }  // namespace ams
@@ -773,7 +785,7 @@ extern "C" AMS_API ams_status ams_sort_small_noalloc(void* d_keys, uint64_t* d_v
   const bool pairs = d_vals != nullptr;
   const int ks = kt == AMS_U64 ? 8 : 4;
   const int tf = kt == AMS_F32 ? 1 : 0;
-  const size_t sm = basecase_smem_bytes(ks, pairs);
+  const size_t sm = basecase_smem_bytes(ks, pairs, false);
   const cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
 #define AMS_LAUNCH_NOALLOC(K, P)                                                               \

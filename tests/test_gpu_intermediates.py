@@ -44,12 +44,13 @@ def _gpu_pieces(seg, starts, piece_of, piece_starts):
 
 @pytest.mark.parametrize("dist", I.DISTRIBUTIONS)
 @pytest.mark.parametrize("kt,bits", [(O.KT_U64, 64), (O.KT_U32, 32)])
-@pytest.mark.parametrize("pairs", [True, False])
-def test_level_intermediates_match_oracle(dist, kt, bits, pairs):
-    n, r, seed = 1 << 20, [16, 16], 3
+@pytest.mark.parametrize("pairs,cap", [(True, 0), (False, 0), (True, 4096)])
+def test_level_intermediates_match_oracle(dist, kt, bits, pairs, cap):
+    # cap 4096 with pairs: the base case of half the capacity (two blocks per SM)
+    n, r, seed = 1 << 20, ([16, 16] if not cap else [16, 32]), 3
     keys = I.generate(dist, n, 17, bits)
     vals = np.arange(n, dtype=np.uint64)
-    C = ams.default_basecase_cap(kt, pairs)
+    C = cap or ams.default_basecase_cap(kt, pairs)
     pl = O.plan(n, kt, 2, r, pairs=pairs, C=C)
     trace = []
     ref = O.ams_sort(kt, keys, pl, seed=seed, trace=trace, vals=vals if pairs else None)
@@ -59,7 +60,7 @@ def test_level_intermediates_match_oracle(dist, kt, bits, pairs):
     if pairs:
         vin = to_dev(vals)
         vout = torch.empty_like(vin)
-        ctx.sort(src, dst, vin, vout, levels=2, buckets=r, seed=seed, kt=kt)
+        ctx.sort(src, dst, vin, vout, levels=2, buckets=r, seed=seed, kt=kt, cap=cap)
     else:
         ctx.sort(src, dst, levels=2, buckets=r, seed=seed, kt=kt)
     ctx.sync()
