@@ -111,17 +111,9 @@ __global__ void __launch_bounds__(512) k_classify(LevelArgs a) {
     const uint32_t b1 = b0 + nv * V;
     // the ids of one 128-bit key vector are stored together when that is aligned
     const bool ids_vec = ((uintptr_t)(ids + b0) % (2 * V)) == 0;
-    // per-thread run-length counting: one shared atomic whenever the bucket changes
-    // (sorted or duplicate-heavy input adds whole runs at once)
-    uint32_t run_id = 0xFFFFFFFFu, run_n = 0;
-    auto count = [&](uint32_t id) {
-      if (id != run_id) {
-        if (run_n) atomicAdd(&hist[run_id], run_n);
-        run_id = id;
-        run_n = 0;
-      }
-      ++run_n;
-    };
+    // one shared atomic per key (measured faster than per-thread run-length counting on
+    // every input tried, sorted and all-equal included)
+    auto count = [&](uint32_t id) { atomicAdd(&hist[id], 1u); };
     auto cls = [&](K x) { return classify<K>(cs, TREE, a.logBp, a.B, order_in<K>(x, a.tf_src)); };
     auto vec = [&](uint32_t v, const uint4& w) {
       K ks[V];
@@ -166,7 +158,6 @@ __global__ void __launch_bounds__(512) k_classify(LevelArgs a) {
       for (uint32_t u = 0; u < U; ++u) vec(v + u * NT, w[u]);
     }
     for (; v < nv; v += NT) vec(v, __ldcs(vp + v));
-    if (run_n) atomicAdd(&hist[run_id], run_n);
     __syncthreads();
     uint32_t* out = a.counts + (size_t)k * a.nid;
     for (uint32_t i = threadIdx.x; i < a.nid; i += NT) out[i] = hist[i];
