@@ -68,10 +68,12 @@ typedef struct ams_options {
   uint32_t overpartition_b; /* b: 0 = 1 for levels == 1, else 4 (Section 6) */
   uint32_t basecase_cap;    /* C: largest group sorted in shared memory;
                                0 = 16384 for 32-bit keys, 8192 otherwise and for pairs,
-                               except a pairs sort of one segment whose planned leaves
-                               (n over the product of the r's, plus 25%) fit 4096: 4096.
-                               Pairs with C <= 4096 use a base case that fits two blocks
-                               per SM. */
+                               except a sort of one segment of more than that many keys
+                               whose planned leaves (n over the product of the r's,
+                               plus 25%) fit half of it: pairs then use 4096, 32-bit
+                               keys 8192.  Pairs with C <= 4096 use a base case that
+                               fits two blocks per SM, 32-bit keys with C <= 8192 one
+                               that holds half as many keys per thread. */
   uint32_t flags;           /* AMS_FLAG_* */
 } ams_options;
 
@@ -415,8 +417,9 @@ AMS_API ams_status ams_sort_small_noalloc(void* d_keys, uint64_t* d_vals, uint64
 
 /* --------------------------------------------------------------- misc */
 AMS_API const char* ams_status_string(ams_status s);
-/* Default base-case capacity for a key type (pairs != 0 for key-value sorts); a pairs
- * sort whose planned leaves fit 4096 keys uses 4096 (see ams_options.basecase_cap). */
+/* Default base-case capacity for a key type (pairs != 0 for key-value sorts); a sort
+ * of one segment whose planned leaves fit half of it may use half (see
+ * ams_options.basecase_cap). */
 AMS_API uint32_t ams_default_basecase_cap(ams_key_type kt, int pairs);
 /* Library version, e.g. "0.1.0". */
 AMS_API const char* ams_version(void);

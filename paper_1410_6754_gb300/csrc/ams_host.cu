@@ -30,7 +30,7 @@ struct Plan {
   uint32_t b = 0, a_fixed = 0, C = 0;
   int ksize = 8;
   bool pairs = false;
-  bool small = false;  // pairs base case of half the capacity (C <= its capacity)
+  bool small = false;  // base case of half the capacity (C <= its capacity)
   uint64_t n = 0, nseg_user = 1;
   uint64_t seg1_cap = 0, bc0_cap = 0, big_cap = 0, tiny_cap = 0;
   LevelPlan lv[kMaxLevels];
@@ -69,11 +69,14 @@ ams_status make_plan(uint64_t n, uint64_t nseg_user, ams_key_type kt, bool pairs
     est = (est + rr.back() - 1) / rr.back();
   }
   p->L = (int)rr.size();
-  // a pairs sort of one segment whose leaves are expected to fit the base case of
-  // half the capacity (with 25% slack for uneven groups) uses it: two blocks per SM
-  if (pairs && !o.basecase_cap && nseg_user == 1 && est * 5 / 4 <= basecase_small_cap())
-    p->C = basecase_small_cap();
-  p->small = pairs && p->C <= basecase_small_cap();
+  // a sort of one segment larger than the capacity whose leaves are expected to fit
+  // the base case of half the capacity (with 25% slack for uneven groups) uses it:
+  // pairs get two blocks per SM, 32-bit keys half the registers per thread (64-bit
+  // keys have no such variant)
+  const uint32_t small_cap = basecase_small_cap(p->ksize, pairs);
+  if (small_cap && !o.basecase_cap && nseg_user == 1 && n > p->C && est * 5 / 4 <= small_cap)
+    p->C = small_cap;
+  p->small = small_cap && p->C <= small_cap;
   // every segment holds at most C keys: level 0 hands them all to the base case and
   // the distribution levels would find no work, so none is launched
   if (n <= p->C) p->L = 0;

@@ -218,7 +218,7 @@ cudaError_t launch_scan(const LevelArgs& a, int grid, bool few_segments, cudaStr
 cudaError_t launch_binpack(const LevelArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_scatter(const LevelArgs& a, int ksize, bool pairs, bool stable, int grid,
                            cudaStream_t s);
-// small: the pairs base case of half the capacity (two blocks per SM)
+// small: the base case of half the capacity (pairs, and 32-bit keys)
 cudaError_t launch_basecase(const BaseArgs& a, int ksize, bool pairs, bool big, int grid, cudaStream_t s,
                             bool small = false);
 cudaError_t launch_tiny(const BaseArgs& a, int ksize, bool pairs, int grid, cudaStream_t s);
@@ -230,6 +230,6 @@ size_t scatter_smem_bytes(int ksize, bool pairs, bool stable, uint32_t B);
 size_t classify_smem_bytes(int ksize, uint32_t B, bool tree);
 size_t basecase_smem_bytes(int ksize, bool pairs, bool small = false);
 uint32_t basecase_max_cap(int ksize, bool pairs);
-uint32_t basecase_small_cap();  // capacity of the small pairs base case
+uint32_t basecase_small_cap(int ksize, bool pairs);  // capacity of the small base case (0: none)
 
 }  // namespace ams

@@ -18,9 +18,10 @@ namespace ams {
 template <typename K, bool PAIRS, bool SMALL = false>
 struct BaseCfg {
   static constexpr int NT = 512;
-  // SMALL (pairs only): half the capacity, so that two blocks fit per SM; used when a
-  // sort's leaves are expected to fit it
-  static constexpr uint32_t CAP = SMALL ? 4096u : (sizeof(K) == 4 && !PAIRS) ? 16384u : 8192u;
+  // SMALL: half the capacity (pairs: two blocks per SM instead of one; 32-bit keys:
+  // half the keys per thread in registers), used when a sort's leaves are expected to
+  // fit it
+  static constexpr uint32_t CAP = SMALL ? (PAIRS ? 4096u : 8192u) : (sizeof(K) == 4 && !PAIRS) ? 16384u : 8192u;
   static constexpr int KPT = CAP / NT;
   static constexpr uint32_t CELLS = 16384;  // 16-bit counters, two per word
   static constexpr uint32_t BIGCELL = 8;    // cells above this size are checked for one value
@@ -665,11 +666,15 @@ size_t basecase_smem_bytes(int ksize, bool pairs, bool small) {
   size_t off[8];
   if (pairs && small)
     return ksize == 4 ? base_smem_layout<uint32_t, true, true>(off) : base_smem_layout<uint64_t, true, true>(off);
+  if (small && ksize == 4) return base_smem_layout<uint32_t, false, true>(off);
   if (ksize == 4) return pairs ? base_smem_layout<uint32_t, true>(off) : base_smem_layout<uint32_t, false>(off);
   return pairs ? base_smem_layout<uint64_t, true>(off) : base_smem_layout<uint64_t, false>(off);
 }
 
-uint32_t basecase_small_cap() { return BaseCfg<uint64_t, true, true>::CAP; }
+uint32_t basecase_small_cap(int ksize, bool pairs) {
+  if (pairs) return BaseCfg<uint64_t, true, true>::CAP;
+  return ksize == 4 ? BaseCfg<uint32_t, false, true>::CAP : 0u;  // (64-bit keys: none)
+}
 
 uint32_t basecase_max_cap(int ksize, bool pairs) {
   if (ksize == 4) return pairs ? BaseCfg<uint32_t, true>::CAP : BaseCfg<uint32_t, false>::CAP;
@@ -678,7 +683,7 @@ uint32_t basecase_max_cap(int ksize, bool pairs) {
 
 cudaError_t launch_basecase(const BaseArgs& a, int ksize, bool pairs, bool big, int grid, cudaStream_t s,
                             bool small) {
-  small = small && pairs;
+  small = small && (pairs || ksize == 4);
   const size_t sm = basecase_smem_bytes(ksize, pairs, small);
   cudaError_t e;
 #define AMS_LAUNCH_BASE(K, P, S)                                                               \
@@ -696,13 +701,14 @@ cudaError_t launch_basecase(const BaseArgs& a, int ksize, bool pairs, bool big, 
     }                                                                                          \
   } while (0)
   if (ksize == 4) {
-    if (small) AMS_LAUNCH_BASE(uint32_t, true, true);
+    if (pairs && small) AMS_LAUNCH_BASE(uint32_t, true, true);
     else if (pairs) AMS_LAUNCH_BASE(uint32_t, true, false);
+    else if (small) AMS_LAUNCH_BASE(uint32_t, false, true);
     else AMS_LAUNCH_BASE(uint32_t, false, false);
   } else {
-    if (small) AMS_LAUNCH_BASE(uint64_t, true, true);
+    if (pairs && small) AMS_LAUNCH_BASE(uint64_t, true, true);
     else if (pairs) AMS_LAUNCH_BASE(uint64_t, true, false);
-    else AMS_LAUNCH_BASE(uint64_t, false, false);
+    else AMS_LAUNCH_BASE(uint64_t, false, false);  // (64-bit keys: no small variant)
   }
 #undef AMS_LAUNCH_BASE
   return cudaGetLastError();
