@@ -131,6 +131,17 @@ AMS_API ams_status ams_sort_pairs_into(const void* d_keys_in, void* d_keys_out,
 AMS_API ams_status ams_sort_host(void* h_keys, uint64_t* h_vals, uint64_t n, ams_key_type kt,
                          int levels, const uint32_t* buckets_per_level, uint64_t seed,
                          const ams_options* opt, void* stream);
+/* Asynchronous host-buffer form on a context (ctx NULL = default context): enqueues on
+ * `stream` the copy of h_keys (and h_vals) into the context's device staging buffer,
+ * the sort, and the copy of the result back into the same host arrays, and returns
+ * once that work is enqueued.  With page-locked host arrays the copies overlap other
+ * streams' work, so sorts on two contexts and two streams keep both directions of the
+ * host link busy.  The host arrays must stay untouched until the stream has passed
+ * the call; device errors are returned by ams_context_sync(ctx).  Reusing a context
+ * is ordered on its stream like every context call (one stream per context). */
+AMS_API ams_status ams_sort_host_async(void* ctx, void* h_keys, uint64_t* h_vals, uint64_t n,
+                               ams_key_type kt, int levels, const uint32_t* buckets_per_level,
+                               uint64_t seed, const ams_options* opt, void* stream);
 
 /* --------------------------------------------------------------- contexts */
 

@@ -93,6 +93,7 @@ _SIGS = {
     "ams_sort_keys_into": (_ST, [_P, _P, _U64, _I, _I, _PU32, _U64, _P, _P]),
     "ams_sort_pairs_into": (_ST, [_P, _P, _P, _P, _U64, _I, _I, _PU32, _U64, _P, _P]),
     "ams_sort_host": (_ST, [_P, _P, _U64, _I, _I, _PU32, _U64, _P, _P]),
+    "ams_sort_host_async": (_ST, [_P, _P, _P, _U64, _I, _I, _PU32, _U64, _P, _P]),
     "ams_context_create": (_ST, [_U64, ctypes.POINTER(ctypes.c_void_p)]),
     "ams_context_destroy": (_ST, [_P]),
     "ams_sort_request": (_ST, [_P, ctypes.POINTER(Request), _P]),
@@ -273,6 +274,25 @@ def sort_host(keys, vals=None, levels=2, buckets=(256, 256), seed=0, a=0, b=0, c
     o = _opts(a, b, cap, flags)
     _check(L.ams_sort_host(kptr, vptr, n, kt, levels, bk, seed, ctypes.byref(o), _stream(stream)),
            "ams_sort_host")
+    return keys if vals is None else (keys, vals)
+
+
+def sort_host_async(keys, vals=None, levels=2, buckets=(256, 256), seed=0, a=0, b=0, cap=0, flags=0,
+                    kt=None, ctx=None, stream=None):
+    """Sort page-locked CPU tensors through the device without waiting
+    (ams_sort_host_async): the copies in, the sort and the copies back are enqueued on
+    `stream` with the scratch of `ctx`; the tensors hold the result once the stream has
+    passed the call (ctx.sync() / stream synchronize)."""
+    assert not keys.is_cuda and keys.is_contiguous()
+    if vals is not None:
+        assert not vals.is_cuda and vals.is_contiguous() and vals.numel() == keys.numel()
+        assert vals.element_size() == 8
+    h = ctx.handle if ctx is not None else None
+    _check(lib().ams_sort_host_async(h, ctypes.c_void_p(keys.data_ptr()),
+                                     ctypes.c_void_p(vals.data_ptr()) if vals is not None else None,
+                                     keys.numel(), key_type(keys, kt), levels, _buckets(buckets), seed,
+                                     ctypes.byref(_opts(a, b, cap, flags)), _stream(stream)),
+           "ams_sort_host_async")
     return keys if vals is None else (keys, vals)
 
 

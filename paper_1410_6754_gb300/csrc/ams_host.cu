@@ -888,15 +888,11 @@ ams_status ams_sort_pairs_into(const void* d_keys_in, void* d_keys_out, const ui
                      stream);
 }
 
-ams_status ams_sort_host(void* h_keys, uint64_t* h_vals, uint64_t n, ams_key_type kt, int levels,
-                         const uint32_t* buckets_per_level, uint64_t seed, const ams_options* opt,
-                         void* stream) {
-  if (!h_keys && n) return AMS_ERR_INVALID;
-  if (n == 0) return AMS_OK;
-  Context* cx = default_context();
-  if (!cx) return AMS_ERR_CUDA;
-  std::lock_guard<std::mutex> lk(cx->mu);
-  const cudaStream_t s = (cudaStream_t)stream;
+// Host arrays -> the context's staging buffer, sort in place there, staging buffer ->
+// host arrays, all enqueued on s (the caller holds cx->mu).
+static ams_status enqueue_host_sort(Context* cx, void* h_keys, uint64_t* h_vals, uint64_t n,
+                                    ams_key_type kt, int levels, const uint32_t* buckets_per_level,
+                                    uint64_t seed, const ams_options* opt, cudaStream_t s) {
   const size_t kb = (size_t)n * ksize_of(kt), vb = h_vals ? (size_t)n * 8 : 0;
   ams_status st = grow(cx, &cx->stage, &cx->stage_bytes, kb + vb + 512);
   if (st != AMS_OK) return st;
@@ -908,8 +904,34 @@ ams_status ams_sort_host(void* h_keys, uint64_t* h_vals, uint64_t n, ams_key_typ
   if ((st = run_sort(cx, &rq, s)) != AMS_OK) return st;
   AMS_TRY(cudaMemcpyAsync(h_keys, dk, kb, cudaMemcpyDeviceToHost, s));
   if (dv) AMS_TRY(cudaMemcpyAsync(h_vals, dv, vb, cudaMemcpyDeviceToHost, s));
+  return AMS_OK;
+}
+
+ams_status ams_sort_host(void* h_keys, uint64_t* h_vals, uint64_t n, ams_key_type kt, int levels,
+                         const uint32_t* buckets_per_level, uint64_t seed, const ams_options* opt,
+                         void* stream) {
+  if (!h_keys && n) return AMS_ERR_INVALID;
+  if (n == 0) return AMS_OK;
+  Context* cx = default_context();
+  if (!cx) return AMS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(cx->mu);
+  const cudaStream_t s = (cudaStream_t)stream;
+  ams_status st = enqueue_host_sort(cx, h_keys, h_vals, n, kt, levels, buckets_per_level, seed, opt, s);
+  if (st != AMS_OK) return st;
   AMS_TRY(cudaStreamSynchronize(s));
   return read_status(cx);
+}
+
+ams_status ams_sort_host_async(void* ctx, void* h_keys, uint64_t* h_vals, uint64_t n, ams_key_type kt,
+                               int levels, const uint32_t* buckets_per_level, uint64_t seed,
+                               const ams_options* opt, void* stream) {
+  if (!h_keys && n) return AMS_ERR_INVALID;
+  if (n == 0) return AMS_OK;
+  Context* cx = ctx_or_default(ctx);
+  if (!cx) return AMS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(cx->mu);
+  return enqueue_host_sort(cx, h_keys, h_vals, n, kt, levels, buckets_per_level, seed, opt,
+                           (cudaStream_t)stream);
 }
 
 ams_status ams_context_create(uint64_t hbm_budget_bytes, void** ctx) {

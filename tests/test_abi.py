@@ -109,6 +109,15 @@ def test_noalloc_refuses_misaligned_views_on_the_host(libpath):
     assert L.ams_sort_small_noalloc(None, None, 0, ams.U32, None) == ams.OK
 
 
+def test_host_async_checks_arguments_on_the_host(libpath):
+    """ams_sort_host_async returns AMS_ERR_INVALID for a null key array with n > 0, and
+    AMS_OK for n = 0, before it touches a context or the GPU."""
+    L = ams.lib()
+    bk = (ctypes.c_uint32 * 2)(16, 16)
+    assert L.ams_sort_host_async(None, None, None, 10, ams.U64, 2, bk, 0, None, None) == ams.ERR_INVALID
+    assert L.ams_sort_host_async(None, None, None, 0, ams.U64, 2, bk, 0, None, None) == ams.OK
+
+
 def test_server_admission_rule(libpath):
     """The serving loop's admission decision (a pure function; no GPU): by the budget of
     scratch in flight, and by the device's free memory when a worker context must grow."""

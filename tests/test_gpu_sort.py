@@ -215,6 +215,32 @@ def test_out_of_place_and_host_entry_points():
     assert same_bits(h, ek) and np.array_equal(hv, ev)
 
 
+@pytest.mark.parametrize("pairs", [False, True])
+def test_host_async_two_contexts_two_streams(pairs):
+    """ams_sort_host_async: six sorts of page-locked host arrays enqueued alternately on
+    two contexts and two streams (each context on its own stream), all in flight at
+    once; every array then holds its own sorted result (pairs: stable)."""
+    ctxs = [ams.Context(), ams.Context()]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    n = (1 << 20) + 77
+    keys = [I.generate(["uniform", "zipf", "sorted"][i % 3], n, 40 + i, 64) for i in range(6)]
+    vals = np.arange(n, dtype=np.uint64)
+    hk = [torch.from_numpy(k.view(np.int64).copy()).pin_memory() for k in keys]
+    hv = [torch.from_numpy(vals.view(np.int64).copy()).pin_memory() for _ in keys] if pairs else [None] * 6
+    for i in range(6):
+        ams.sort_host_async(hk[i], hv[i], levels=2, buckets=[64, 64], seed=i, kt=O.KT_U64,
+                            ctx=ctxs[i % 2], stream=streams[i % 2])
+    for c in ctxs:
+        c.sync()
+    for i in range(6):
+        ek, ev = O.sort_pairs(O.KT_U64, keys[i], vals)
+        assert same_bits(hk[i].numpy().view(np.uint64), ek), i
+        if pairs:
+            assert np.array_equal(hv[i].numpy().view(np.uint64), ev), i
+    for c in ctxs:
+        c.close()
+
+
 @pytest.mark.parametrize("kt,bits,dist", [(O.KT_U64, 64, "uniform"), (O.KT_U32, 32, "uniform"),
                                           (O.KT_F32, 32, None), (O.KT_U64, 64, "zipf")])
 @pytest.mark.parametrize("in_off,out_off", [(1, 3), (2, 1), (3, 2)])
