@@ -341,9 +341,9 @@ AMS_API ams_status ams_rlm_sort(void* ctx, const void* d_keys_in, void* d_keys_o
  * way): for (key type, pairs, ceil(log2 n)) it times candidate plans on n synthetic
  * uniform keys and on n duplicate-heavy keys (P(rank k) ~ 1/k over 2^20 values) in
  * ctx's scratch (ctx NULL = default context), scoring a plan by the sum of its two
- * times.  Round 1 picks the shape: 1, 2 or 3 distribution levels, groups per level r
+ * times.  A first pass picks the shape: 1, 2 or 3 distribution levels, groups per level r
  * a power of two near (n / t)^(1/levels) for target leaf sizes t = C/2 and C/4, at
- * the default a and b.  Round 2 tries, on that shape, b = 16 with the default a
+ * the default a and b.  A second pass tries, on that shape, b = 16 with the default a
  * (Section 7.2's b = 16, a = 1.6 log10 n), a = 1 with b = 64 (the appendix's sweep),
  * a = 1 with the default b, a = 1 with b = 16 (each while b * r <= 2048) and half the
  * base-case capacity C.  The fastest plan is kept in a table shared by the process
