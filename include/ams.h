@@ -137,8 +137,9 @@ AMS_API ams_status ams_sort_host(void* h_keys, uint64_t* h_vals, uint64_t n, ams
  * once that work is enqueued.  With page-locked host arrays the copies overlap other
  * streams' work, so sorts on two contexts and two streams keep both directions of the
  * host link busy.  The host arrays must stay untouched until the stream has passed
- * the call; device errors are returned by ams_context_sync(ctx).  Reusing a context
- * is ordered on its stream like every context call (one stream per context). */
+ * the call; device errors are returned by ams_context_sync(ctx).  When the call itself
+ * returns an error, the copies it had enqueued have finished.  Reusing a context is
+ * ordered on its stream like every context call (one stream per context). */
 AMS_API ams_status ams_sort_host_async(void* ctx, void* h_keys, uint64_t* h_vals, uint64_t n,
                                ams_key_type kt, int levels, const uint32_t* buckets_per_level,
                                uint64_t seed, const ams_options* opt, void* stream);

@@ -889,7 +889,9 @@ ams_status ams_sort_pairs_into(const void* d_keys_in, void* d_keys_out, const ui
 }
 
 // Host arrays -> the context's staging buffer, sort in place there, staging buffer ->
-// host arrays, all enqueued on s (the caller holds cx->mu).
+// host arrays, all enqueued on s (the caller holds cx->mu).  When a step fails after
+// the first copy was enqueued, the stream is drained before the error is returned, so
+// that no copy still reads or writes the caller's arrays once the call has returned.
 static ams_status enqueue_host_sort(Context* cx, void* h_keys, uint64_t* h_vals, uint64_t n,
                                     ams_key_type kt, int levels, const uint32_t* buckets_per_level,
                                     uint64_t seed, const ams_options* opt, cudaStream_t s) {
@@ -898,12 +900,18 @@ static ams_status enqueue_host_sort(Context* cx, void* h_keys, uint64_t* h_vals,
   if (st != AMS_OK) return st;
   void* dk = cx->stage;
   uint64_t* dv = h_vals ? (uint64_t*)(cx->stage + ((kb + 255) & ~(size_t)255)) : nullptr;
-  AMS_TRY(cudaMemcpyAsync(dk, h_keys, kb, cudaMemcpyHostToDevice, s));
-  if (dv) AMS_TRY(cudaMemcpyAsync(dv, h_vals, vb, cudaMemcpyHostToDevice, s));
+  auto fail = [&](ams_status e) {
+    cudaStreamSynchronize(s);
+    return e;
+  };
+  cudaError_t ce = cudaMemcpyAsync(dk, h_keys, kb, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess && dv) ce = cudaMemcpyAsync(dv, h_vals, vb, cudaMemcpyHostToDevice, s);
+  if (ce != cudaSuccess) return fail(cuda_status(ce));
   ams_request rq = make_req(dk, dk, dv, dv, n, kt, levels, buckets_per_level, seed, opt);
-  if ((st = run_sort(cx, &rq, s)) != AMS_OK) return st;
-  AMS_TRY(cudaMemcpyAsync(h_keys, dk, kb, cudaMemcpyDeviceToHost, s));
-  if (dv) AMS_TRY(cudaMemcpyAsync(h_vals, dv, vb, cudaMemcpyDeviceToHost, s));
+  if ((st = run_sort(cx, &rq, s)) != AMS_OK) return fail(st);
+  ce = cudaMemcpyAsync(h_keys, dk, kb, cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess && dv) ce = cudaMemcpyAsync(h_vals, dv, vb, cudaMemcpyDeviceToHost, s);
+  if (ce != cudaSuccess) return fail(cuda_status(ce));
   return AMS_OK;
 }
 
