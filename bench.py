@@ -190,7 +190,7 @@ def run_reference(args, wl):
         "config": {"workload": wl["desc"], "sample_keys_per_step": m},
         "cpu_baseline": {"value": value, "unit": "keys/s", "cores": 1, "kind": "oracle",
                          "sample": f"{m} keys of the same workload per step (first {m} keys of the "
-                                   f"seeded input), numpy stable sort, one thread"},
+                                   f"seeded input), numpy stable sort, one thread", **_cpu_info()},
         "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
