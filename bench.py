@@ -712,7 +712,8 @@ def run_ams(args, wl):
                "d2h_bytes_per_step": n * w, "steps": args.e2e_steps,
                "api": "ams_sort_host (pinned host buffers, copies inside the timed region)"}
         del host
-        e2e["pipelined"] = _e2e_pipelined(ams, host_src, dst, kw, max(args.e2e_steps, 8), dist, world, n, w)
+        if world == 1:  # (8 page-locked copies of the input per rank: one process only)
+            e2e["pipelined"] = _e2e_pipelined(ams, host_src, dst, kw, max(args.e2e_steps, 8), dist, world, n, w)
         del host_src
 
     plain = None
